@@ -1,0 +1,300 @@
+"""Pins of the CPU oracle against facts fixed by the paper and by mathematics.
+
+Each check is chosen so that a plausible mistake in the oracle (a dropped chord test,
+a wrong label comparison, an off-by-one in the length bound, a wrong hash constant)
+fails at least one of them:
+  * counts printed in Table 1 of the paper (tests/golden/table1_synthetic.txt);
+  * closed forms: C_n, K_n, K_{a,b}, wheels, grids, trees, unicyclic graphs (Section 2);
+  * the definition itself, by brute force over vertex subsets, on hundreds of seeded graphs;
+  * an independent library enumerator (networkx) where it is installed;
+  * the level sets T_t against their definition by brute force over vertex sequences;
+  * degree labellings worked by hand (tests/golden/degree_labeling.txt);
+  * the published SplitMix64 sequence behind the cycle hash (tests/golden/splitmix64.txt).
+"""
+import itertools
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1410_4876_gb300 import inputs as I
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+# ------------------------------------------------------------------ hash
+
+def test_splitmix64_known_answer():
+    lines = [l for l in open(os.path.join(GOLDEN, "splitmix64.txt")) if l.strip() and not l.startswith("#")]
+    seed = int(lines[0].split()[1])
+    expect = [int(x) for x in lines[1:]]
+    got, s = [], seed
+    for _ in expect:
+        v, s = oracle.splitmix64_next(s)
+        got.append(v)
+    assert got == expect
+
+
+def test_vertex_hash_is_splitmix_draw():
+    # r(v) is the SplitMix64 output for state (v + 1) * GAMMA, i.e. draw v of the seed-0 stream.
+    s = 0
+    for v in range(50):
+        out, s = oracle.splitmix64_next(s)
+        assert oracle.vertex_hash(v) == out
+
+
+def test_cycle_hash_is_set_function():
+    c = [5, 9, 2, 7]
+    h = oracle.cycle_hash(c)
+    for perm in itertools.permutations(c):
+        assert oracle.cycle_hash(list(perm)) == h
+    assert oracle.cycle_hash([5, 9, 2]) != h
+    assert oracle.cycle_hash([5, 9, 2, 8]) != h
+
+
+# ------------------------------------------------------------------ degree labelling
+
+def _golden_labelings():
+    out = []
+    for line in open(os.path.join(GOLDEN, "degree_labeling.txt")):
+        if not line.strip() or line.startswith("#"):
+            continue
+        name, n, edges, labels = [x.strip() for x in line.split("|")]
+        e = [tuple(int(v) for v in x.split("-")) for x in edges.split()]
+        out.append((name, int(n), e, [int(x) for x in labels.split()]))
+    return out
+
+
+@pytest.mark.parametrize("name,n,edges,labels", _golden_labelings())
+def test_degree_labeling_golden(name, n, edges, labels):
+    g = I.from_edges(n, edges)
+    assert oracle.degree_labeling(g).tolist() == labels
+
+
+def _check_labeling_property(g, lab):
+    # Section 2: l(u_i) = i where u_i has minimum degree in G_i = G - {u_1..u_{i-1}};
+    # ties go to the smallest id.
+    order = np.argsort(lab)
+    alive = set(range(g.n))
+    adj = [set(g.col[g.row_ptr[v]:g.row_ptr[v + 1]].tolist()) for v in range(g.n)]
+    for u in order.tolist():
+        degs = {v: len(adj[v] & alive) for v in alive}
+        dmin = min(degs.values())
+        assert degs[u] == dmin
+        assert u == min(v for v in alive if degs[v] == dmin)
+        alive.remove(u)
+
+
+@pytest.mark.parametrize("seed", range(20))
+def test_degree_labeling_property(seed):
+    g = I.gnp(12 + seed % 7, 0.3, seed)
+    lab = oracle.degree_labeling(g)
+    assert sorted(lab.tolist()) == list(range(1, g.n + 1))
+    _check_labeling_property(g, lab)
+
+
+# ------------------------------------------------------------------ Table 1
+
+def _table1(speed):
+    rows = []
+    for line in open(os.path.join(GOLDEN, "table1_synthetic.txt")):
+        if not line.strip() or line.startswith("#"):
+            continue
+        fam, args, n, m, dmax, c3, clc, sp = line.split()
+        if sp != speed:
+            continue
+        a = tuple(int(x) for x in args.split(","))
+        rows.append((fam, a, int(n), int(m), int(dmax), int(c3), int(clc)))
+    return rows
+
+
+def _family(fam, a):
+    return {"cycle": I.cycle, "wheel": I.wheel, "kab": I.complete_bipartite, "grid": I.grid}[fam](*a)
+
+
+def _check_table1(fam, a, n, m, dmax, c3, clc):
+    g = _family(fam, a)
+    assert (g.n, g.m, g.max_degree) == (n, m, dmax)
+    r = oracle.enumerate_cycles(g)
+    assert int(r.hist[3]) == c3
+    assert r.total - int(r.hist[3]) == clc
+
+
+@pytest.mark.parametrize("fam,a,n,m,dmax,c3,clc", _table1("fast"))
+def test_table1(fam, a, n, m, dmax, c3, clc):
+    _check_table1(fam, a, n, m, dmax, c3, clc)
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("fam,a,n,m,dmax,c3,clc", _table1("slow"))
+def test_table1_slow(fam, a, n, m, dmax, c3, clc):
+    _check_table1(fam, a, n, m, dmax, c3, clc)
+
+
+# ------------------------------------------------------------------ closed forms
+
+@pytest.mark.parametrize("n", [3, 4, 5, 7, 16, 33, 64, 65, 130])
+def test_cycle_graph(n):
+    r = oracle.enumerate_cycles(I.cycle(n))
+    assert r.total == 1 and int(r.hist[n]) == 1
+    # one chordless path of every length 3..n-1 grows around the cycle
+    assert r.tcount[3:n].tolist() == [1] * (n - 3)
+
+
+@pytest.mark.parametrize("n", [3, 4, 5, 8, 12])
+def test_complete_graph(n):
+    r = oracle.enumerate_cycles(I.complete(n))
+    assert int(r.hist[3]) == math.comb(n, 3) and r.total == math.comb(n, 3)
+    assert int(r.tcount.sum()) == 0
+
+
+@pytest.mark.parametrize("a,b", [(2, 2), (2, 5), (3, 3), (4, 7), (8, 8), (6, 2)])
+def test_complete_bipartite(a, b):
+    r = oracle.enumerate_cycles(I.complete_bipartite(a, b))
+    assert int(r.hist[4]) == math.comb(a, 2) * math.comb(b, 2) == r.total
+
+
+@pytest.mark.parametrize("n", [4, 5, 9, 40])
+def test_wheel(n):
+    r = oracle.enumerate_cycles(I.wheel(n))
+    assert int(r.hist[3]) == n and int(r.hist[n]) == 1 and r.total == n + 1
+
+
+@pytest.mark.parametrize("k,l", [(2, 2), (2, 7), (3, 3), (3, 5), (4, 4)])
+def test_grid_squares(k, l):
+    r = oracle.enumerate_cycles(I.grid(k, l))
+    assert int(r.hist[4]) == (k - 1) * (l - 1)
+    if (k, l) == (3, 3):
+        assert r.total == 5 and int(r.hist[8]) == 1
+    if k == 2:
+        # a ladder: any cycle through two non-neighbouring rungs has the rungs between
+        # them as chords, so the squares are the only chordless cycles
+        assert r.total == l - 1
+
+
+@pytest.mark.parametrize("seed", range(10))
+def test_tree_has_no_triplets(seed):
+    g = I.random_tree(5 + 3 * seed, seed)
+    r = oracle.enumerate_cycles(g)
+    assert r.total == 0 and int(r.tcount.sum()) == 0 and oracle.triplet_count(g) == 0
+
+
+@pytest.mark.parametrize("seed", range(10))
+def test_unicyclic_has_one_triplet(seed):
+    # Section 2: a graph with a unique cycle has |T(G)| = 1 (or the cycle is a triangle)
+    g = I.random_unicyclic(6 + 3 * seed, seed)
+    r = oracle.enumerate_cycles(g)
+    assert r.total == 1
+    assert oracle.triplet_count(g) == (0 if int(r.hist[3]) == 1 else 1)
+
+
+@pytest.mark.parametrize("seed", range(10))
+def test_triplet_bound(seed):
+    # Section 2: |T(G)| <= (Delta - 1) * m / 2
+    g = I.gnp(30, 0.2, seed)
+    assert oracle.triplet_count(g) <= (g.max_degree - 1) * g.m / 2
+
+
+# ------------------------------------------------------------------ brute force
+
+def _small_graphs(count, seed0=0):
+    out = []
+    for s in range(count):
+        n = 4 + s % 11
+        p = [0.15, 0.3, 0.5, 0.7][s % 4]
+        out.append(I.gnp(n, p, seed0 + s))
+    return out
+
+
+@pytest.mark.parametrize("chunk", range(6))
+def test_algorithm1_equals_definition(chunk):
+    for g in _small_graphs(60, 1000 * chunk):
+        a = oracle.enumerate_cycles(g, cycles=True)
+        b = oracle.bruteforce(g, cycles=True)
+        assert a.hist.tolist() == b.hist.tolist(), g.name
+        assert a.hash == b.hash, g.name
+        assert sorted(a.cycles) == sorted(b.cycles), g.name
+        assert len(set(a.cycles)) == len(a.cycles)  # each cycle exactly once
+        assert sum(oracle.cycle_hash(c) for c in b.cycles) % 2 ** 64 == b.hash
+
+
+@pytest.mark.parametrize("max_len", [1, 2, 3, 4, 5, 7])
+def test_length_bound_equals_definition(max_len):
+    for g in _small_graphs(40, 77):
+        a = oracle.enumerate_cycles(g, max_len=max_len)
+        b = oracle.bruteforce(g, max_len=max_len)
+        assert a.hist.tolist() == b.hist.tolist() and a.hash == b.hash
+
+
+def test_named_small_graphs_equal_definition():
+    for g in [I.grid(3, 4), I.grid(4, 4), I.complete_bipartite(3, 4), I.wheel(7), I.complete(6),
+              I.cycle(9), I.path(6), I.empty(5), I.grid(2, 9), I.complete_bipartite(2, 8)]:
+        a = oracle.enumerate_cycles(g, cycles=True)
+        b = oracle.bruteforce(g, cycles=True)
+        assert sorted(a.cycles) == sorted(b.cycles) and a.hash == b.hash
+
+
+def test_networkx_enumerator():
+    nx = pytest.importorskip("networkx")
+    if not hasattr(nx, "chordless_cycles"):
+        pytest.skip("networkx without chordless_cycles")
+    for g in _small_graphs(40, 555) + [I.grid(4, 4), I.wheel(6), I.complete_bipartite(3, 3)]:
+        G = nx.Graph()
+        G.add_nodes_from(range(g.n))
+        G.add_edges_from(g.edges().tolist())
+        ref = sorted(tuple(sorted(c)) for c in nx.chordless_cycles(G))
+        a = oracle.enumerate_cycles(g, cycles=True)
+        assert sorted(tuple(sorted(c)) for c in a.cycles) == ref
+
+
+def _level_sets_by_definition(g, lab, L):
+    """T_t by its definition: induced paths <v_1..v_t> (no edge between non-consecutive
+    vertices) with l(v_2) minimal and l(v_1) < l(v_3), for 3 <= t < L."""
+    adj = [set(g.col[g.row_ptr[v]:g.row_ptr[v + 1]].tolist()) for v in range(g.n)]
+    counts = [0] * (L + 1)
+    for t in range(3, L):
+        for seq in itertools.permutations(range(g.n), t):
+            if any(seq[i + 1] not in adj[seq[i]] for i in range(t - 1)):
+                continue
+            if any(seq[j] in adj[seq[i]] for i in range(t) for j in range(i + 2, t)):
+                continue
+            if min(lab[v] for v in seq) != lab[seq[1]] or not lab[seq[0]] < lab[seq[2]]:
+                continue
+            counts[t] += 1
+    return counts
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_level_counts_equal_definition(seed):
+    g = [I.gnp(7, 0.45, seed), I.grid(2, 4), I.wheel(5), I.complete_bipartite(3, 3),
+         I.gnp(8, 0.35, 100 + seed), I.cycle(7), I.grid(3, 3), I.gnp(8, 0.25, 200 + seed)][seed]
+    lab = oracle.degree_labeling(g)
+    r = oracle.enumerate_cycles(g)
+    assert r.tcount.tolist() == _level_sets_by_definition(g, lab, g.n)
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_relabelling_invariance(seed):
+    # Section 2: the labelling fixes each cycle's orientation uniquely for ANY bijection,
+    # so renaming vertices (which changes the tie-breaks of the degree labelling) maps the
+    # cycle set onto itself.
+    g = I.gnp(18, 0.25, seed)
+    perm = I.random_permutation(g.n, seed + 1000)
+    gp = I.permute(g, perm)
+    a = oracle.enumerate_cycles(g, cycles=True)
+    b = oracle.enumerate_cycles(gp, cycles=True)
+    assert a.hist.tolist() == b.hist.tolist()
+    mapped = sorted(tuple(sorted(int(perm[v]) for v in c)) for c in a.cycles)
+    assert mapped == sorted(tuple(sorted(c)) for c in b.cycles)
+
+
+@pytest.mark.parametrize("nparts", [2, 3, 7])
+def test_parts_add_up(nparts):
+    g = I.gnp(30, 0.2, 5)
+    whole = oracle.enumerate_cycles(g)
+    parts = [oracle.enumerate_cycles(g, part=p, nparts=nparts) for p in range(nparts)]
+    assert sum(p.hist for p in parts).tolist() == whole.hist.tolist()
+    assert sum(p.tcount for p in parts).tolist() == whole.tcount.tolist()
+    assert sum(p.hash for p in parts) % 2 ** 64 == whole.hash
