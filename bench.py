@@ -1,0 +1,327 @@
+"""Benchmark: chordless cycles/s (and paths expanded/s) on one GB300.
+
+Default workload (one step): full enumeration of the 8 x 8 grid graph and of the seeded
+Erdos-Renyi graph G(n=60, p=0.15, seed 7), all cycle lengths, through the C ABI
+(cc_enumerate on graphs already resident in HBM).  Between timed steps the L2 cache is
+flushed by writing a 512 MiB buffer.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload grid8+gnp60|grid6|gnm2000|batch]
+
+--impl reference times the CPU oracle (Algorithm 1 in plain C, test infrastructure) on
+the host cores for the same workload and metric.  Under torchrun (N > 1) every rank runs
+its own replica of the workload (independent problems, no collective): weak scaling.
+Rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1410_4876_gb300 import inputs as I  # noqa: E402
+
+WORKLOADS = {
+    "grid8+gnp60": ("grid 8x8 (64 vertices, 112 edges, row-major ids) + Erdos-Renyi G(n=60, p=0.15, seed 7); "
+                    "all chordless cycles of every length", lambda: [(I.grid(8, 8), 0), (I.gnp(60, 0.15, 7), 0)]),
+    "grid6": ("grid 6x6 (36 vertices, 60 edges), all lengths", lambda: [(I.grid(6, 6), 0)]),
+    "gnm2000": ("G(n=2000, m=4000, seed 11), cycles up to 12 vertices", lambda: [(I.gnm(2000, 4000, 11), 12)]),
+}
+
+
+def algorithmic_bytes(r) -> int:
+    """Bytes the expansion kernel must move: every stored path is read once and every
+    path after the initial triplets is written once.  Record sizes: bitset, n <= 64:
+    B (8) + H (8) + M (4) = 20 bytes; n <= 128: 28; n <= 256: 44; CSR: 2 bytes per vertex."""
+    tc = r.tcount
+    if r.info.mode == 2:
+        per = np.arange(tc.size, dtype=np.int64) * 2
+        return int((tc.astype(np.int64) * per).sum() * 2 - int(tc[3]) * 6) if tc.size > 3 else 0
+    n = len(r.hist) - 1
+    rec = 20 if n <= 64 else (28 if n <= 128 else 44)
+    return rec * (2 * int(tc.sum()) - int(tc[3]))
+
+
+def _env_rank():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("LOCAL_RANK", "0"))
+
+
+def _dist_init(world):
+    if world <= 1:
+        return None
+    import torch.distributed as dist
+    dist.init_process_group("nccl" if _has_cuda() else "gloo")
+    return dist
+
+
+def _has_cuda():
+    try:
+        import torch
+        return torch.cuda.is_available()
+    except Exception:
+        return False
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx = max(mx, float(f[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def cpu_baseline(work, seconds_hint=True, parts_per_core=2, sample_parts=None):
+    """The oracle as it stands, run over the workload's initial triplets split across all
+    host cores (threads; ctypes releases the GIL).  ``sample_parts`` limits the run to a
+    subset of the parts (a bounded sample)."""
+    import concurrent.futures as cf
+
+    import oracle
+    cores = os.cpu_count() or 1
+    nparts = cores * parts_per_core
+    parts = list(range(nparts)) if sample_parts is None else sample_parts
+    t0 = time.perf_counter()
+    cyc = paths = 0
+    with cf.ThreadPoolExecutor(cores) as ex:
+        for g, L in work:
+            res = list(ex.map(lambda p: oracle.enumerate_cycles(g, max_len=L, part=p, nparts=nparts), parts))
+            cyc += sum(r.total for r in res)
+            paths += sum(int(r.tcount.sum()) for r in res)
+    dt = time.perf_counter() - t0
+    return cyc, paths, dt, cores, len(parts), nparts
+
+
+def run_reference(args, work, desc):
+    rank, world, _ = _env_rank()
+    if rank != 0:
+        return
+    cores = os.cpu_count() or 1
+    nparts = cores * 2
+    # each step: a quarter of the triplet parts (rotating), on all host cores
+    for w in range(args.warmup):
+        cpu_baseline(work, sample_parts=list(range(w % 4, nparts, 4)))
+    tot_c = tot_p = 0
+    tot_t = 0.0
+    for s in range(args.steps):
+        c, p, dt, _, _, _ = cpu_baseline(work, sample_parts=list(range(s % 4, nparts, 4)))
+        tot_c += c
+        tot_p += p
+        tot_t += dt
+    value = tot_c / tot_t if tot_t > 0 else 0.0
+    line = {
+        "impl": "reference", "metric": "chordless cycles/s", "value": value, "unit": "cycles/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * tot_t / max(args.steps, 1),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": desc, "sample": "each step: every 4th of the initial-triplet parts (rotating)"},
+        "paths_expanded_per_s": tot_p / tot_t if tot_t > 0 else 0.0,
+        "cpu_baseline": {"value": value, "unit": "cycles/s", "cores": cores, "kind": "oracle",
+                         "sample": f"{nparts} triplet parts, a quarter per step, {cores} threads"},
+        "e2e": {"value": value, "unit": "cycles/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, work, desc):
+    import torch
+
+    from paper_1410_4876_gb300 import cc
+    rank, world, local = _env_rank()
+    dist = _dist_init(world)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    # run on torch's stream so events, the L2 flush and the library share one stream
+    ctx = cc.Context(frontier_bytes=8 << 30, stream=stream.cuda_stream)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    loaded = [(ctx.load(g), L, g) for g, L in work]
+
+    def step():
+        res = [lg.enumerate(L) for lg, L, _ in loaded]
+        return res
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    cycles = paths = 0
+    eng_ms = 0.0
+    eng_bytes = 0
+    launches = 0
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        for k in range(args.steps):
+            flush.zero_()
+            ev[k][0].record(stream)
+            res = step()
+            ev[k][1].record(stream)
+            for r in res:
+                cycles += r.total
+                paths += r.paths
+                eng_ms += r.info.ms_engine
+                eng_bytes += algorithmic_bytes(r)
+                launches += 3  # labelling, seeding, persistent expansion
+        torch.cuda.synchronize()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    t_ms = float(sum(step_ms))
+    if dist:
+        tt = torch.tensor([t_ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_ms = float(tt.item())
+        dist.barrier()
+    value = world * cycles / (t_ms / 1000.0)
+
+    # end to end through the public API: H2D of the CSR from pinned memory (cc_graph_load),
+    # enumeration, D2H of the results, free
+    pinned = []
+    for g, L in work:
+        rp = torch.from_numpy(g.row_ptr.astype(np.uint32).view(np.int32)).pin_memory()
+        cl = torch.from_numpy(g.col.astype(np.uint32).view(np.int32)).pin_memory()
+        pinned.append((g, L, rp.numpy().view(np.uint32), cl.numpy().view(np.uint32)))
+    h2d = sum(4 * (rp.size + cl.size) for _, _, rp, cl in pinned)
+    d2h = sum(8 * (2 * ((L or g.n) + 1) + 1) for g, L, _, _ in pinned)
+    torch.cuda.synchronize()
+    e2e_steps = max(1, min(args.steps, 10))
+    t0 = time.perf_counter()
+    ecyc = 0
+    for _ in range(e2e_steps):
+        for g, L, rp, cl in pinned:
+            s, h = cc.cc_graph_load(ctx.handle, g.n, rp, cl)
+            assert s == cc.CC_OK
+            s, hist, hh, tc, _, info = cc.cc_enumerate(h, g.n, L)
+            assert s == cc.CC_OK
+            ecyc += int(hist.sum())
+            cc.cc_graph_free(h)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    e2e_value = world * ecyc / e2e_s
+
+    peak, peak_kind = _peaks()
+    achieved = eng_bytes / (eng_ms / 1000.0) / 1e9 if eng_ms > 0 else 0.0
+    traffic = _ncu_traffic()
+    line = {
+        "metric": "chordless cycles/s", "value": value, "unit": "cycles/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": desc, "l2": "flushed between steps (512 MiB write)",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                   "cycles_per_step": cycles // args.steps, "paths_per_step": paths // args.steps},
+        "paths_expanded_per_s": world * paths / (t_ms / 1000.0),
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak if peak else None, "traffic": traffic,
+                     "kernel": "engine_kernel (persistent expansion)", "peak_kind": peak_kind,
+                     "algorithmic_bytes_per_step": eng_bytes // args.steps, "kernel_ms_per_step": eng_ms / args.steps},
+        "e2e": {"value": e2e_value, "unit": "cycles/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "steps": e2e_steps},
+        "gpu_launches": launches,
+        "clocks": clk.summary(),
+    }
+    if rank == 0 and not args.no_cpu:
+        c, p, dt, cores, nsel, nparts = cpu_baseline(work, sample_parts=None)
+        line["cpu_baseline"] = {"value": c / dt, "unit": "cycles/s", "cores": cores, "kind": "oracle",
+                                "sample": f"whole workload, {nparts} triplet parts on {cores} threads, {dt:.1f} s"}
+    for lg, _, _ in loaded:
+        lg.close()
+    ctx.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def _ncu_traffic():
+    """DRAM bytes per launch of the expansion kernel from the committed ncu summary, when
+    the summary was taken on the current kernel (the summary records it); else None."""
+    p = os.path.join(ROOT, "profiles", "engine_bitset1_grid8_gnp60.json")
+    if not os.path.exists(p):
+        return None
+    try:
+        d = json.load(open(p))
+        return d.get("dram_bytes_per_step")
+    except Exception:
+        return None
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="grid8+gnp60", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-cpu", action="store_true", help="skip the cpu_baseline leg")
+    args = ap.parse_args()
+    desc, make = WORKLOADS[args.workload]
+    work = make()
+    if args.impl == "reference":
+        run_reference(args, work, desc)
+    else:
+        run_ours(args, work, desc)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,209 @@
+/*
+ * cc.h - C ABI of the GB300 (sm_103a) chordless-cycle enumeration library.
+ *
+ * Method: arXiv 1410.4876 (Jradi, Dias, Castonguay, Longo, do Nascimento), "A GPU-based
+ * parallel algorithm for enumerating all chordless cycles in graphs".
+ *   - problem statement: Section 1 (a chordless cycle is an induced subgraph that is a
+ *     cycle of a finite undirected simple graph) and the input/output of Algorithm 1;
+ *   - degree labelling: Section 2;
+ *   - initial triplets and triangles: Section 4.3 and Algorithm 2;
+ *   - level-by-level path expansion with the label, chord and close tests: Section 4.4
+ *     and Algorithm 3, driven by the relaunch loop of Algorithm 4;
+ *   - count-only operation: the footnote of Table 1 (Grid 8x10).
+ *
+ * Conventions used throughout this header
+ *   - Length counts vertices.  A cycle of k vertices has k edges; a path <v1..vt> has t.
+ *   - max_len bounds the cycle length; 0 means no bound.  L' = min(max_len, n) when
+ *     max_len > 0, else n.
+ *   - hist[k] (k = 0..L') is the number of chordless cycles with k vertices; entries 0..2
+ *     are always zero.  total = sum of hist; it INCLUDES triangles (the paper's Table 1
+ *     prints triangles in column C3 and longer cycles in column #clc).
+ *   - Cycle hash (order independent, exact, defined by this library because the paper
+ *     prints no cycle lists): with mix() the SplitMix64 output finaliser (Steele, Lea and
+ *     Flood 2014, constants of Vigna's splitmix64.c) and GAMMA = 0x9E3779B97F4A7C15,
+ *         r(v)  = mix((v + 1) * GAMMA)              v = caller's vertex id
+ *         h(C)  = mix(sum_{v in C} r(v) + |C| * GAMMA)
+ *         hash  = sum over all chordless cycles C of h(C)
+ *     all modulo 2^64.  A chordless cycle is determined by its vertex set (it is induced),
+ *     so h depends on the set only.  A sum (not XOR) makes a duplicated report visible.
+ *   - tcount[t] (optional output) is the number of chordless paths of t vertices that the
+ *     expansion stored (the sets T of Algorithm 1 by length, t = 3..L'-1).  These depend on
+ *     the degree labelling's tie rule; this library breaks ties by smallest vertex id.
+ *   - Canonical ordered cycle (cycle lists): start at the smallest vertex id and continue
+ *     towards the smaller of its two cycle neighbours.
+ *
+ * Ownership: every pointer argument is HOST memory owned by the caller unless stated
+ * otherwise; the library copies what it needs.  Device memory is owned by the context
+ * (or supplied by the caller through cc_options.workspace).  Nothing here aborts or traps:
+ * every failure is a status code.  All device waits are bounded and report
+ * CC_ERR_TIMEOUT.  There is no CPU fallback: without a usable sm_103a device the calls
+ * that need one fail with CC_ERR_CUDA.
+ *
+ * Thread safety: a context and the graphs loaded into it must be used from one host
+ * thread at a time.
+ */
+#ifndef CC_H_
+#define CC_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t cc_status;
+
+#define CC_OK 0
+#define CC_PENDING 1              /* cc_batch_poll: not finished within the timeout       */
+#define CC_ERR_ARG (-1)           /* bad argument (NULL where required, size mismatch)    */
+#define CC_ERR_INVALID_GRAPH (-2) /* CSR is not a simple undirected graph                 */
+#define CC_ERR_OOM (-3)           /* device or host allocation failed                     */
+#define CC_ERR_CUDA (-4)          /* a CUDA call failed (no device, launch error, ...)    */
+#define CC_ERR_TIMEOUT (-5)       /* a bounded device wait gave up                        */
+#define CC_ERR_TRUNCATED (-6)     /* cycle list buffer too small; required sizes returned */
+#define CC_ERR_UNSUPPORTED (-7)   /* graph beyond this build's limits (see cc_limits)     */
+#define CC_ERR_CAPACITY (-8)      /* frontier memory too small to make progress           */
+
+#define CC_MODE_AUTO 0   /* bitset adjacency when n <= 256, CSR adjacency otherwise */
+#define CC_MODE_BITSET 1 /* force the shared-memory bitset path (n <= 256)          */
+#define CC_MODE_CSR 2    /* force the CSR path (any n up to the CSR limit)          */
+
+typedef struct cc_context cc_context;
+typedef struct cc_graph cc_graph;
+
+/* Options of a context.  Zero-initialise and set what you need. */
+typedef struct cc_options {
+  uint64_t frontier_bytes;     /* device bytes for chordless paths in flight; 0 = default  */
+                               /* (min(16 GiB, 40% of free memory)).  When a level would   */
+                               /* not fit, the expansion switches to depth-first chunks.  */
+  void* stream;                /* cudaStream_t to run on; NULL = a stream the context owns */
+  void* workspace;             /* optional caller-owned device buffer (>= 256-byte aligned)*/
+  uint64_t workspace_bytes;    /* used as the frontier arena instead of an allocation      */
+  uint32_t threads_per_block;  /* expansion kernel block size (128..1024, multiple of 32) */
+  uint32_t blocks_per_sm;      /* persistent blocks per SM; 0 = occupancy limit (max 4)   */
+  uint32_t mode;               /* CC_MODE_*                                               */
+  uint32_t spin_limit;         /* grid-barrier wait limit in polls; 0 = default (~8 s)    */
+} cc_options;
+
+/* Build limits. */
+typedef struct cc_limits {
+  uint32_t max_n_bitset;  /* largest n of the bitset path                         */
+  uint32_t max_n_csr;     /* largest n of the CSR path                            */
+  uint32_t max_n_batch;   /* largest n of a graph in cc_batch_submit              */
+  uint32_t max_batch;     /* largest number of graphs in one cc_batch_submit      */
+} cc_limits;
+
+/* Timings and counters of the last cc_enumerate on a context. */
+typedef struct cc_run_info {
+  double ms_proc;          /* device time: labelling, seeding, expansion, reductions  */
+  double ms_total;         /* ms_proc plus the result copies back to the host         */
+  double ms_engine;        /* device time of the expansion kernel alone                */
+  uint64_t steps;          /* expansion steps (levels, or chunks when spilling)       */
+  uint64_t paths;          /* chordless paths stored (sum of tcount)                  */
+  uint64_t cycles;         /* chordless cycles found (sum of hist)                    */
+  uint32_t mode;           /* CC_MODE_BITSET or CC_MODE_CSR                           */
+  uint32_t grid_blocks;    /* persistent grid size                                    */
+  uint32_t spilled;        /* 1 if some level was expanded in depth-first chunks      */
+  uint32_t pad;
+  uint64_t peak_bytes;     /* largest arena extent in use                             */
+} cc_run_info;
+
+/* Optional cycle list.  Set the capacities and pointers; the call fills count,
+ * total_vertices and, if both fit, offsets[0..count] and vertices[0..total_vertices).
+ * If they do not fit, cc_enumerate returns CC_ERR_TRUNCATED with the required count and
+ * total_vertices filled in (hist and hash are still valid); call again with larger buffers.
+ * Cycle order in the list is unspecified; each cycle is in canonical order (above). */
+typedef struct cc_cycles {
+  uint64_t capacity_cycles;    /* in: offsets has capacity_cycles + 1 entries   */
+  uint64_t capacity_vertices;  /* in: vertices has capacity_vertices entries    */
+  uint64_t* offsets;           /* out: cycle i is vertices[offsets[i] .. offsets[i+1]) */
+  uint32_t* vertices;          /* out: original vertex ids                      */
+  uint64_t count;              /* out: number of cycles                         */
+  uint64_t total_vertices;     /* out: sum of cycle lengths                     */
+} cc_cycles;
+
+/* Create a context on the current CUDA device.  opts may be NULL (all defaults).
+ * Errors: CC_ERR_ARG (out NULL, bad option values), CC_ERR_CUDA (no usable device). */
+cc_status cc_context_create(const cc_options* opts, cc_context** out);
+
+/* Wait for outstanding work and free everything the context owns. NULL is ignored. */
+void cc_context_destroy(cc_context* ctx);
+
+/* Human-readable name of a status code (static string). */
+const char* cc_status_str(cc_status s);
+
+/* Fill the build limits. */
+void cc_get_limits(cc_limits* out);
+
+/*
+ * Load a graph (Section 4.2: the compact representation V_e/E_e).
+ *   n        number of vertices (ids 0..n-1)
+ *   row_ptr  host array of n+1 offsets, row_ptr[0] = 0, non-decreasing
+ *   col_idx  host array of row_ptr[n] neighbour ids; every undirected edge appears in both
+ *            rows.  Rows need not be sorted (they are sorted on load).
+ * The graph must be simple: no self-loops, no duplicate neighbours, symmetric adjacency,
+ * ids < n; otherwise CC_ERR_INVALID_GRAPH.  Isolated vertices and several components are
+ * fine.  n larger than cc_limits.max_n_csr gives CC_ERR_UNSUPPORTED.  The CSR is copied to
+ * the device; the caller may free its arrays after the call returns.
+ */
+cc_status cc_graph_load(cc_context* ctx, uint32_t n, const uint32_t* row_ptr,
+                        const uint32_t* col_idx, cc_graph** out);
+
+/* Free a loaded graph. NULL is ignored. */
+void cc_graph_free(cc_graph* g);
+
+/* Vertex and edge counts and maximum degree of a loaded graph (any pointer may be NULL). */
+cc_status cc_graph_info(const cc_graph* g, uint32_t* n, uint64_t* m, uint32_t* max_degree);
+
+/*
+ * Enumerate all chordless cycles of a loaded graph with at most max_len vertices.
+ *   out_hist    host array of L'+1 entries (L' as above); required
+ *   out_hash    host pointer to one uint64; required
+ *   out_tcount  host array of L'+1 entries, or NULL
+ *   out_cycles  cycle list, or NULL for count-only operation
+ *   out_info    timings and counters, or NULL
+ * Blocks the calling thread until the result is on the host.  Errors: CC_ERR_ARG,
+ * CC_ERR_CUDA, CC_ERR_TIMEOUT, CC_ERR_CAPACITY (frontier memory below the minimum of
+ * about L' * max_degree paths), CC_ERR_TRUNCATED (see cc_cycles).
+ */
+cc_status cc_enumerate(cc_graph* g, uint32_t max_len, uint64_t* out_hist, uint64_t* out_hash,
+                       uint64_t* out_tcount, cc_cycles* out_cycles, cc_run_info* out_info);
+
+/*
+ * Batched enumeration: `count` graphs packed back to back, all enumerated by one
+ * persistent launch whose frontier mixes paths of every graph.
+ *   n[g]        vertices of graph g (each <= cc_limits.max_n_batch)
+ *   row_off[g]  index of graph g's first row offset in row_ptr (count+1 entries; graph g
+ *               owns row_ptr[row_off[g] .. row_off[g] + n[g]], its own offsets from 0)
+ *   col_off[g]  index of graph g's first neighbour in col_idx (count+1 entries)
+ * The inputs are validated and copied before the call returns; the work runs
+ * asynchronously on the context's stream.  One batch may be outstanding per context.
+ * Errors: CC_ERR_ARG, CC_ERR_INVALID_GRAPH (the index of the first bad graph is stored
+ * in *out_batch), CC_ERR_UNSUPPORTED, CC_ERR_CUDA.
+ */
+typedef uint64_t cc_batch_id;
+cc_status cc_batch_submit(cc_context* ctx, uint32_t count, const uint32_t* n,
+                          const uint64_t* row_off, const uint32_t* row_ptr,
+                          const uint64_t* col_off, const uint32_t* col_idx, uint32_t max_len,
+                          cc_batch_id* out_batch);
+
+/*
+ * Wait up to timeout_us microseconds for a batch.  CC_PENDING if it is still running
+ * (call again), otherwise its final status; on CC_OK the outputs are filled:
+ *   hist        count * hist_stride entries; graph g's histogram at hist[g * hist_stride],
+ *               entries 0..min(L'_g, hist_stride - 1); hist_stride >= 65 holds every length
+ *   hash        count entries
+ *   paths       count entries (stored paths per graph), or NULL
+ *   done_us     count entries: microseconds from the start of the batch's expansion until
+ *               the step that finished the graph's last path, or NULL
+ *   info        whole-batch timings, or NULL
+ */
+cc_status cc_batch_poll(cc_context* ctx, cc_batch_id batch, uint32_t timeout_us, uint64_t* hist,
+                        uint32_t hist_stride, uint64_t* hash, uint64_t* paths, double* done_us,
+                        cc_run_info* info);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CC_H_ */

@@ -177,3 +177,15 @@ def bruteforce(g, max_len: int = 0, cycles: bool = False) -> Result:
         if nc.value <= cap_c and nv.value <= cap_v:
             return Result(hist, int(h.value), None, _cycles_from(offs, verts, nc.value))
         cap_c, cap_v = max(cap_c, nc.value), max(cap_v, nv.value)
+
+
+def enumerate_parallel(g, max_len: int = 0, threads: int = 0) -> Result:
+    """Algorithm 1 split over the initial triplets (index modulo ``threads``) and run on a
+    thread pool; ctypes releases the GIL during each call.  Sums the parts."""
+    import concurrent.futures as cf
+    threads = threads or os.cpu_count() or 1
+    with cf.ThreadPoolExecutor(threads) as ex:
+        parts = list(ex.map(lambda p: enumerate_cycles(g, max_len, part=p, nparts=threads), range(threads)))
+    hist = sum(p.hist for p in parts)
+    tcount = sum(p.tcount for p in parts)
+    return Result(hist, sum(p.hash for p in parts) % (1 << 64), tcount, None)

@@ -1,0 +1,342 @@
+"""ctypes binding of the C ABI in ``include/cc.h`` (argument marshalling only).
+
+The functions keep the C names (``cc_context_create``, ``cc_graph_load``, ``cc_enumerate``,
+``cc_batch_submit``, ``cc_batch_poll`` ...).  Every step of the enumeration runs in the
+CUDA library; this module only converts numpy arrays to pointers.  There is no CPU
+fallback: if the library is missing, loading it raises.
+
+PyTorch is used for plumbing only: ``Context(use_torch=True)`` hands the library a
+frontier arena allocated by torch's caching allocator and torch's current CUDA stream.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+from typing import List, Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libcc.so")
+
+CC_OK = 0
+CC_PENDING = 1
+CC_ERR_ARG = -1
+CC_ERR_INVALID_GRAPH = -2
+CC_ERR_OOM = -3
+CC_ERR_CUDA = -4
+CC_ERR_TIMEOUT = -5
+CC_ERR_TRUNCATED = -6
+CC_ERR_UNSUPPORTED = -7
+CC_ERR_CAPACITY = -8
+
+CC_MODE_AUTO = 0
+CC_MODE_BITSET = 1
+CC_MODE_CSR = 2
+
+_u32p = ctypes.POINTER(ctypes.c_uint32)
+_u64p = ctypes.POINTER(ctypes.c_uint64)
+_dblp = ctypes.POINTER(ctypes.c_double)
+
+
+class cc_options(ctypes.Structure):
+    _fields_ = [
+        ("frontier_bytes", ctypes.c_uint64),
+        ("stream", ctypes.c_void_p),
+        ("workspace", ctypes.c_void_p),
+        ("workspace_bytes", ctypes.c_uint64),
+        ("threads_per_block", ctypes.c_uint32),
+        ("blocks_per_sm", ctypes.c_uint32),
+        ("mode", ctypes.c_uint32),
+        ("spin_limit", ctypes.c_uint32),
+    ]
+
+
+class cc_limits(ctypes.Structure):
+    _fields_ = [
+        ("max_n_bitset", ctypes.c_uint32),
+        ("max_n_csr", ctypes.c_uint32),
+        ("max_n_batch", ctypes.c_uint32),
+        ("max_batch", ctypes.c_uint32),
+    ]
+
+
+class cc_run_info(ctypes.Structure):
+    _fields_ = [
+        ("ms_proc", ctypes.c_double),
+        ("ms_total", ctypes.c_double),
+        ("ms_engine", ctypes.c_double),
+        ("steps", ctypes.c_uint64),
+        ("paths", ctypes.c_uint64),
+        ("cycles", ctypes.c_uint64),
+        ("mode", ctypes.c_uint32),
+        ("grid_blocks", ctypes.c_uint32),
+        ("spilled", ctypes.c_uint32),
+        ("pad", ctypes.c_uint32),
+        ("peak_bytes", ctypes.c_uint64),
+    ]
+
+
+class cc_cycles(ctypes.Structure):
+    _fields_ = [
+        ("capacity_cycles", ctypes.c_uint64),
+        ("capacity_vertices", ctypes.c_uint64),
+        ("offsets", _u64p),
+        ("vertices", _u32p),
+        ("count", ctypes.c_uint64),
+        ("total_vertices", ctypes.c_uint64),
+    ]
+
+
+class CCError(RuntimeError):
+    def __init__(self, status: int, what: str = ""):
+        self.status = status
+        super().__init__(f"{what}: {status_str(status)} ({status})" if what else f"{status_str(status)} ({status})")
+
+
+_lib = None
+
+# exported symbols and their ctypes signatures (the C names of include/cc.h)
+SIGNATURES = {
+    "cc_context_create": (ctypes.c_int32, [ctypes.POINTER(cc_options), ctypes.POINTER(ctypes.c_void_p)]),
+    "cc_context_destroy": (None, [ctypes.c_void_p]),
+    "cc_status_str": (ctypes.c_char_p, [ctypes.c_int32]),
+    "cc_get_limits": (None, [ctypes.POINTER(cc_limits)]),
+    "cc_graph_load": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_uint32, _u32p, _u32p, ctypes.POINTER(ctypes.c_void_p)]),
+    "cc_graph_free": (None, [ctypes.c_void_p]),
+    "cc_graph_info": (ctypes.c_int32, [ctypes.c_void_p, _u32p, _u64p, _u32p]),
+    "cc_enumerate": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_uint32, _u64p, _u64p, _u64p,
+                                      ctypes.POINTER(cc_cycles), ctypes.POINTER(cc_run_info)]),
+    "cc_batch_submit": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_uint32, _u32p, _u64p, _u32p, _u64p, _u32p,
+                                         ctypes.c_uint32, _u64p]),
+    "cc_batch_poll": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32, _u64p, ctypes.c_uint32,
+                                       _u64p, _u64p, _dblp, ctypes.POINTER(cc_run_info)]),
+}
+
+
+def load_library(path: Optional[str] = None):
+    """Load the CUDA library (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or LIB_PATH
+    if not os.path.exists(path):
+        raise ImportError(f"CUDA library not built: {path} (run __graft_entry__.build())")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def status_str(s: int) -> str:
+    try:
+        return load_library().cc_status_str(s).decode()
+    except ImportError:
+        return str(s)
+
+
+def _p32(a: np.ndarray):
+    return a.ctypes.data_as(_u32p)
+
+
+def _p64(a: np.ndarray):
+    return a.ctypes.data_as(_u64p)
+
+
+def _check(s: int, what: str):
+    if s != CC_OK:
+        raise CCError(s, what)
+
+
+def cc_get_limits() -> cc_limits:
+    lim = cc_limits()
+    load_library().cc_get_limits(ctypes.byref(lim))
+    return lim
+
+
+def cc_context_create(opts: Optional[cc_options] = None) -> ctypes.c_void_p:
+    h = ctypes.c_void_p()
+    _check(load_library().cc_context_create(ctypes.byref(opts) if opts is not None else None, ctypes.byref(h)),
+           "cc_context_create")
+    return h
+
+
+def cc_context_destroy(ctx) -> None:
+    load_library().cc_context_destroy(ctx)
+
+
+def cc_graph_load(ctx, n: int, row_ptr: np.ndarray, col_idx: np.ndarray):
+    rp = np.ascontiguousarray(row_ptr, dtype=np.uint32)
+    cl = np.ascontiguousarray(col_idx, dtype=np.uint32)
+    if cl.size == 0:
+        cl = np.zeros(1, dtype=np.uint32)
+    h = ctypes.c_void_p()
+    s = load_library().cc_graph_load(ctx, n, _p32(rp), _p32(cl), ctypes.byref(h))
+    return s, h
+
+
+def cc_graph_free(g) -> None:
+    load_library().cc_graph_free(g)
+
+
+def cc_enumerate(g, n: int, max_len: int = 0, tcount: bool = True, cycles_capacity: Optional[tuple] = None):
+    """Returns (status, hist, hash, tcount, cycles, info); cycles is a list of tuples or None."""
+    L = n if (max_len == 0 or max_len > n) else max_len
+    hist = np.zeros(L + 1, dtype=np.uint64)
+    tc = np.zeros(L + 1, dtype=np.uint64) if tcount else None
+    hsh = ctypes.c_uint64(0)
+    info = cc_run_info()
+    cyc = None
+    offs = verts = None
+    if cycles_capacity is not None:
+        cap_c, cap_v = cycles_capacity
+        offs = np.zeros(cap_c + 1, dtype=np.uint64)
+        verts = np.zeros(max(cap_v, 1), dtype=np.uint32)
+        cyc = cc_cycles(cap_c, cap_v, _p64(offs), _p32(verts), 0, 0)
+    s = load_library().cc_enumerate(g, max_len, _p64(hist), ctypes.byref(hsh), _p64(tc) if tc is not None else None,
+                                    ctypes.byref(cyc) if cyc is not None else None, ctypes.byref(info))
+    out_cycles = None
+    if cyc is not None:
+        if s == CC_OK:
+            out_cycles = [tuple(int(x) for x in verts[offs[i]:offs[i + 1]]) for i in range(cyc.count)]
+        elif s == CC_ERR_TRUNCATED:
+            out_cycles = (int(cyc.count), int(cyc.total_vertices))
+    return s, hist, int(hsh.value), tc, out_cycles, info
+
+
+def cc_batch_submit(ctx, graphs: Sequence, max_len: int = 0):
+    from .inputs import pack
+    ns, row_off, rp, col_off, cl = pack(graphs)
+    if cl.size == 0:
+        cl = np.zeros(1, dtype=np.uint32)
+    bid = ctypes.c_uint64(0)
+    s = load_library().cc_batch_submit(ctx, len(graphs), _p32(ns), _p64(row_off), _p32(rp), _p64(col_off), _p32(cl),
+                                       max_len, ctypes.byref(bid))
+    return s, int(bid.value)
+
+
+def cc_batch_poll(ctx, batch: int, count: int, timeout_us: int = 0, hist_stride: int = 65):
+    hist = np.zeros((count, hist_stride), dtype=np.uint64)
+    hsh = np.zeros(count, dtype=np.uint64)
+    paths = np.zeros(count, dtype=np.uint64)
+    done = np.zeros(count, dtype=np.float64)
+    info = cc_run_info()
+    s = load_library().cc_batch_poll(ctx, batch, timeout_us, _p64(hist), hist_stride, _p64(hsh), _p64(paths),
+                                     done.ctypes.data_as(_dblp), ctypes.byref(info))
+    return s, hist, hsh, paths, done, info
+
+
+# ------------------------------------------------------------------ convenience layer
+
+@dataclass
+class Result:
+    hist: np.ndarray
+    hash: int
+    tcount: Optional[np.ndarray]
+    cycles: Optional[List[tuple]]
+    info: cc_run_info
+
+    @property
+    def total(self) -> int:
+        return int(self.hist.sum())
+
+    @property
+    def paths(self) -> int:
+        return int(self.tcount.sum()) if self.tcount is not None else int(self.info.paths)
+
+
+class Context:
+    """Owns a cc_context.  With ``use_torch`` the frontier arena comes from torch's
+    caching allocator and the work runs on torch's current stream."""
+
+    def __init__(self, frontier_bytes: int = 0, mode: int = CC_MODE_AUTO, threads_per_block: int = 0,
+                 blocks_per_sm: int = 0, spin_limit: int = 0, use_torch: bool = False, stream: int = 0):
+        self._ws = None
+        opts = cc_options()
+        opts.frontier_bytes = frontier_bytes
+        opts.mode = mode
+        opts.threads_per_block = threads_per_block
+        opts.blocks_per_sm = blocks_per_sm
+        opts.spin_limit = spin_limit
+        opts.stream = stream or None
+        if use_torch:
+            import torch
+            nbytes = frontier_bytes or (1 << 30)
+            self._ws = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+            opts.workspace = self._ws.data_ptr()
+            opts.workspace_bytes = nbytes
+            opts.stream = torch.cuda.current_stream().cuda_stream
+        self.handle = cc_context_create(opts)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            cc_context_destroy(self.handle)
+            self.handle = None
+        self._ws = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def load(self, graph) -> "LoadedGraph":
+        s, h = cc_graph_load(self.handle, graph.n, graph.row_ptr, graph.col)
+        _check(s, "cc_graph_load")
+        return LoadedGraph(self, h, graph.n)
+
+    def enumerate(self, graph, max_len: int = 0, cycles: bool = False) -> Result:
+        with self.load(graph) as g:
+            return g.enumerate(max_len, cycles)
+
+    def batch(self, graphs: Sequence, max_len: int = 0, timeout_s: float = 600.0):
+        """Submit a batch and wait for it; returns (hist[count, 65], hash[count], paths[count],
+        done_us[count], info)."""
+        s, bid = cc_batch_submit(self.handle, graphs, max_len)
+        _check(s, "cc_batch_submit")
+        import time
+        t_end = time.time() + timeout_s
+        while True:
+            s, hist, hsh, paths, done, info = cc_batch_poll(self.handle, bid, len(graphs), 200000)
+            if s != CC_PENDING:
+                break
+            if time.time() > t_end:
+                raise CCError(CC_ERR_TIMEOUT, "cc_batch_poll")
+        _check(s, "cc_batch_poll")
+        return hist, hsh, paths, done, info
+
+
+class LoadedGraph:
+    def __init__(self, ctx: Context, handle, n: int):
+        self.ctx, self.handle, self.n = ctx, handle, n
+
+    def enumerate(self, max_len: int = 0, cycles: bool = False) -> Result:
+        cap = (1024, 8192) if cycles else None
+        while True:
+            s, hist, h, tc, cyc, info = cc_enumerate(self.handle, self.n, max_len, True, cap)
+            if cycles and s == CC_ERR_TRUNCATED:
+                cap = (int(cyc[0]) + 16, int(cyc[1]) + 64)
+                continue
+            _check(s, "cc_enumerate")
+            return Result(hist, h, tc, cyc, info)
+
+    def close(self):
+        if self.handle:
+            cc_graph_free(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

@@ -1,0 +1,814 @@
+// Host implementation of the C ABI declared in include/cc.h.
+//
+// A call of cc_enumerate runs, on the context's stream and without host round trips:
+//   label kernel  (degree labelling, Section 2; relabelled adjacency and hash table)
+//   seed kernel   (initial triplets and triangles, Section 4.3 / Algorithm 2)
+//   engine        (persistent cooperative kernel: every expansion level, Section 4.4 /
+//                  Algorithms 3 and 4, with the bounded-frontier depth-first fallback)
+// followed by one device-to-host copy of the histogram, hash, level counts and status.
+#include <algorithm>
+#include <chrono>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <thread>
+#include <vector>
+
+#include "../../include/cc.h"
+#include "cc_internal.cuh"
+
+using namespace cc;
+
+namespace {
+
+constexpr unsigned int kDefaultSpin = 1u << 25;   // ~8 s of polling at 256 ns
+constexpr unsigned long long kDefaultFrontierCap = 16ull << 30;
+
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+}  // namespace
+
+struct cc_context {
+  int device = 0;
+  int sms = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  cc_options opts{};
+  unsigned char* arena = nullptr;
+  unsigned long long arena_bytes = 0;
+  bool own_arena = false;
+  Control* ctl = nullptr;
+  Frame* frames = nullptr;
+  unsigned int frames_cap = 0;
+  // per-call result buffers (device) and their pinned host mirrors
+  unsigned long long* d_res = nullptr;  // hist | tcount | hash, grown on demand
+  size_t d_res_words = 0;
+  unsigned long long* h_res = nullptr;
+  size_t h_res_words = 0;
+  Control* h_ctl = nullptr;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev2 = nullptr, ev3 = nullptr;
+  cc_run_info last{};
+  // batch state
+  struct Batch {
+    cc_batch_id id = 0;
+    bool active = false;
+    unsigned int count = 0;
+    unsigned int max_len = 0;
+    std::vector<unsigned int> L;  // L' per graph
+    void* d_pack = nullptr;       // packed CSR + per-slot tables
+    size_t d_pack_bytes = 0;
+    unsigned long long* d_hist = nullptr;
+    unsigned long long* d_hash = nullptr;
+    unsigned long long* d_tcount = nullptr;
+    unsigned int* d_last = nullptr;
+    unsigned long long* d_ts = nullptr;
+    unsigned int ts_cap = 0;
+    cc_status status = CC_OK;
+    int grid = 0;
+  } batch;
+  cc_batch_id next_batch = 1;
+};
+
+struct cc_graph {
+  cc_context* ctx = nullptr;
+  unsigned int n = 0;
+  unsigned long long m = 0;
+  unsigned int maxdeg = 0;
+  unsigned int* d_row = nullptr;    // original CSR (sorted rows)
+  unsigned int* d_col = nullptr;
+  unsigned int* d_perm = nullptr;   // [2n]: new->orig, orig->new
+  unsigned long long* d_adj = nullptr;  // bitset rows (n <= 256), W words per row
+  int W = 0;
+  unsigned long long* d_rtab = nullptr;
+  unsigned int* d_nrow = nullptr;   // relabelled CSR
+  unsigned short* d_ncol = nullptr;
+  size_t nrow_bytes = 0, ncol_bytes = 0, adj_bytes = 0, rtab_bytes = 0;
+};
+
+// ------------------------------------------------------------------ helpers
+
+static cc_status cuda_status(cudaError_t e) {
+  if (e == cudaSuccess) return CC_OK;
+  if (e == cudaErrorMemoryAllocation) return CC_ERR_OOM;
+  return CC_ERR_CUDA;
+}
+
+#define CC_CUDA(call)                              \
+  do {                                             \
+    cudaError_t e_ = (call);                       \
+    if (e_ != cudaSuccess) {                       \
+      (void)cudaGetLastError();                    \
+      return cuda_status(e_);                      \
+    }                                              \
+  } while (0)
+
+static unsigned long long r16(unsigned long long x) { return (x + 15) & ~15ull; }
+
+static cc_status dev_alloc(cc_context* c, void** p, size_t bytes) {
+  *p = nullptr;
+  if (bytes == 0) bytes = 16;
+  CC_CUDA(cudaMallocAsync(p, bytes, c->stream));
+  return CC_OK;
+}
+static void dev_free(cc_context* c, void* p) {
+  if (p) cudaFreeAsync(p, c->stream);
+}
+
+static cc_status ensure_results(cc_context* c, size_t words) {
+  if (c->d_res_words < words) {
+    dev_free(c, c->d_res);
+    c->d_res = nullptr;
+    c->d_res_words = 0;
+    cc_status s = dev_alloc(c, (void**)&c->d_res, words * 8);
+    if (s) return s;
+    c->d_res_words = words;
+  }
+  if (c->h_res_words < words) {
+    if (c->h_res) cudaFreeHost(c->h_res);
+    c->h_res = nullptr;
+    c->h_res_words = 0;
+    CC_CUDA(cudaMallocHost((void**)&c->h_res, words * 8));
+    c->h_res_words = words;
+  }
+  return CC_OK;
+}
+
+static cc_status ensure_frames(cc_context* c, unsigned int depth) {
+  if (c->frames_cap >= depth) return CC_OK;
+  dev_free(c, c->frames);
+  c->frames = nullptr;
+  c->frames_cap = 0;
+  unsigned int cap = std::max(depth, 256u);
+  cc_status s = dev_alloc(c, (void**)&c->frames, sizeof(Frame) * cap);
+  if (s) return s;
+  c->frames_cap = cap;
+  return CC_OK;
+}
+
+static cc_status ensure_arena(cc_context* c) {
+  if (c->arena) return CC_OK;
+  if (c->opts.workspace) {
+    if ((reinterpret_cast<uintptr_t>(c->opts.workspace) & 255) || c->opts.workspace_bytes < (1u << 20))
+      return CC_ERR_ARG;
+    c->arena = static_cast<unsigned char*>(c->opts.workspace);
+    c->arena_bytes = c->opts.workspace_bytes & ~255ull;
+    c->own_arena = false;
+    return CC_OK;
+  }
+  unsigned long long want = c->opts.frontier_bytes;
+  if (want == 0) {
+    size_t fr = 0, tot = 0;
+    CC_CUDA(cudaMemGetInfo(&fr, &tot));
+    want = std::min<unsigned long long>(kDefaultFrontierCap, (unsigned long long)(fr * 0.4));
+  }
+  want &= ~255ull;
+  if (want < (1u << 16)) return CC_ERR_ARG;
+  void* p = nullptr;
+  CC_CUDA(cudaMalloc(&p, want));
+  c->arena = static_cast<unsigned char*>(p);
+  c->arena_bytes = want;
+  c->own_arena = true;
+  return CC_OK;
+}
+
+static int engine_grid(cc_context* c, Kind kind, int block, size_t smem) {
+  int bps = 0;
+  if (engine_occupancy(kind, block, smem, &bps) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return 0;
+  }
+  unsigned int want = c->opts.blocks_per_sm ? c->opts.blocks_per_sm : 4u;
+  bps = std::min<int>(bps, (int)want);
+  return bps * c->sms;
+}
+
+// Validate a CSR (Section 1: finite undirected simple graph) and return sorted rows.
+static cc_status validate_csr(unsigned int n, const uint32_t* row_ptr, const uint32_t* col,
+                              std::vector<uint32_t>& sorted, unsigned int* maxdeg) {
+  if (!row_ptr) return CC_ERR_ARG;
+  if (row_ptr[0] != 0) return CC_ERR_INVALID_GRAPH;
+  for (unsigned int v = 0; v < n; ++v)
+    if (row_ptr[v + 1] < row_ptr[v]) return CC_ERR_INVALID_GRAPH;
+  const uint32_t nnz = row_ptr[n];
+  if (nnz && !col) return CC_ERR_ARG;
+  sorted.assign(col, col + nnz);
+  unsigned int md = 0;
+  for (unsigned int v = 0; v < n; ++v) {
+    auto b = sorted.begin() + row_ptr[v], e = sorted.begin() + row_ptr[v + 1];
+    std::sort(b, e);
+    for (auto it = b; it != e; ++it) {
+      if (*it >= n || *it == v) return CC_ERR_INVALID_GRAPH;
+      if (it != b && *it == *(it - 1)) return CC_ERR_INVALID_GRAPH;
+    }
+    md = std::max(md, (unsigned int)(row_ptr[v + 1] - row_ptr[v]));
+  }
+  for (unsigned int v = 0; v < n; ++v)
+    for (uint32_t e = row_ptr[v]; e < row_ptr[v + 1]; ++e) {
+      const uint32_t w = sorted[e];
+      if (!std::binary_search(sorted.begin() + row_ptr[w], sorted.begin() + row_ptr[w + 1], v))
+        return CC_ERR_INVALID_GRAPH;
+    }
+  *maxdeg = md;
+  return CC_OK;
+}
+
+static cc_status map_dev_err(int err) {
+  switch (err) {
+    case kDevOk: return CC_OK;
+    case kDevTimeout: return CC_ERR_TIMEOUT;
+    case kDevCapacity: return CC_ERR_CAPACITY;
+    case kDevSeedCap: return CC_ERR_CAPACITY;
+    default: return CC_ERR_CUDA;
+  }
+}
+
+// ------------------------------------------------------------------ context
+
+extern "C" cc_status cc_context_create(const cc_options* opts, cc_context** out) {
+  if (!out) return CC_ERR_ARG;
+  *out = nullptr;
+  cc_options o{};
+  if (opts) o = *opts;
+  if (o.threads_per_block && (o.threads_per_block < 128 || o.threads_per_block > 512 || o.threads_per_block % 32))
+    return CC_ERR_ARG;
+  if (o.mode > CC_MODE_CSR) return CC_ERR_ARG;
+  int dev = 0;
+  CC_CUDA(cudaGetDevice(&dev));
+  cudaDeviceProp prop;
+  CC_CUDA(cudaGetDeviceProperties(&prop, dev));
+  if (!prop.cooperativeLaunch) return CC_ERR_CUDA;
+  cc_context* c = new cc_context();
+  c->device = dev;
+  c->sms = prop.multiProcessorCount;
+  c->opts = o;
+  if (o.stream) {
+    c->stream = static_cast<cudaStream_t>(o.stream);
+  } else {
+    if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      delete c;
+      return CC_ERR_CUDA;
+    }
+    c->own_stream = true;
+  }
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+    unsigned long long thr = ~0ull;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+  }
+  if (dev_alloc(c, (void**)&c->ctl, sizeof(Control)) != CC_OK ||
+      cudaMallocHost((void**)&c->h_ctl, sizeof(Control)) != cudaSuccess ||
+      cudaEventCreate(&c->ev0) != cudaSuccess || cudaEventCreate(&c->ev1) != cudaSuccess ||
+      cudaEventCreate(&c->ev2) != cudaSuccess || cudaEventCreate(&c->ev3) != cudaSuccess) {
+    (void)cudaGetLastError();
+    cc_context_destroy(c);
+    return CC_ERR_CUDA;
+  }
+  *out = c;
+  return CC_OK;
+}
+
+extern "C" void cc_context_destroy(cc_context* c) {
+  if (!c) return;
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  auto& b = c->batch;
+  dev_free(c, b.d_pack);
+  dev_free(c, c->d_res);
+  dev_free(c, c->frames);
+  dev_free(c, c->ctl);
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  if (c->own_arena && c->arena) cudaFree(c->arena);
+  if (c->h_res) cudaFreeHost(c->h_res);
+  if (c->h_ctl) cudaFreeHost(c->h_ctl);
+  if (c->ev0) cudaEventDestroy(c->ev0);
+  if (c->ev1) cudaEventDestroy(c->ev1);
+  if (c->ev2) cudaEventDestroy(c->ev2);
+  if (c->ev3) cudaEventDestroy(c->ev3);
+  if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+  (void)cudaGetLastError();
+  delete c;
+}
+
+extern "C" const char* cc_status_str(cc_status s) {
+  switch (s) {
+    case CC_OK: return "ok";
+    case CC_PENDING: return "pending";
+    case CC_ERR_ARG: return "invalid argument";
+    case CC_ERR_INVALID_GRAPH: return "not a simple undirected graph";
+    case CC_ERR_OOM: return "out of memory";
+    case CC_ERR_CUDA: return "CUDA error";
+    case CC_ERR_TIMEOUT: return "device wait timed out";
+    case CC_ERR_TRUNCATED: return "cycle list truncated";
+    case CC_ERR_UNSUPPORTED: return "graph beyond supported limits";
+    case CC_ERR_CAPACITY: return "frontier memory too small";
+  }
+  return "unknown status";
+}
+
+extern "C" void cc_get_limits(cc_limits* out) {
+  if (!out) return;
+  out->max_n_bitset = kBitsetMaxN;
+  out->max_n_csr = kCsrMaxN;
+  out->max_n_batch = kMultiMaxN;
+  out->max_batch = kMultiMaxSlots;
+}
+
+// ------------------------------------------------------------------ graphs
+
+extern "C" cc_status cc_graph_load(cc_context* c, uint32_t n, const uint32_t* row_ptr, const uint32_t* col_idx,
+                                   cc_graph** out) {
+  if (!c || !out) return CC_ERR_ARG;
+  *out = nullptr;
+  if (n > kCsrMaxN) return CC_ERR_UNSUPPORTED;
+  std::vector<uint32_t> sorted;
+  unsigned int md = 0;
+  cc_status s = validate_csr(n, row_ptr, col_idx, sorted, &md);
+  if (s) return s;
+  cc_graph* g = new cc_graph();
+  g->ctx = c;
+  g->n = n;
+  g->m = row_ptr[n] / 2;
+  g->maxdeg = md;
+  g->W = n <= 64 ? 1 : (n <= 128 ? 2 : (n <= 256 ? 4 : 0));
+  const unsigned int npad = (n + 1) & ~1u;
+  g->nrow_bytes = r16(4ull * (n + 1));
+  g->ncol_bytes = r16(2ull * row_ptr[n]);
+  g->rtab_bytes = r16(8ull * npad);
+  g->adj_bytes = g->W ? r16(8ull * npad * g->W) : 0;
+  auto fail = [&](cc_status st) {
+    cc_graph_free(g);
+    return st;
+  };
+  if ((s = dev_alloc(c, (void**)&g->d_row, 4ull * (n + 1)))) return fail(s);
+  if ((s = dev_alloc(c, (void**)&g->d_col, 4ull * std::max<uint32_t>(row_ptr[n], 1)))) return fail(s);
+  if ((s = dev_alloc(c, (void**)&g->d_perm, 8ull * std::max<uint32_t>(n, 1)))) return fail(s);
+  if ((s = dev_alloc(c, (void**)&g->d_rtab, g->rtab_bytes))) return fail(s);
+  if ((s = dev_alloc(c, (void**)&g->d_nrow, g->nrow_bytes))) return fail(s);
+  if ((s = dev_alloc(c, (void**)&g->d_ncol, g->ncol_bytes))) return fail(s);
+  if (g->W && (s = dev_alloc(c, (void**)&g->d_adj, g->adj_bytes))) return fail(s);
+  if (cudaMemcpyAsync(g->d_row, row_ptr, 4ull * (n + 1), cudaMemcpyHostToDevice, c->stream) != cudaSuccess ||
+      (row_ptr[n] && cudaMemcpyAsync(g->d_col, sorted.data(), 4ull * row_ptr[n], cudaMemcpyHostToDevice,
+                                     c->stream) != cudaSuccess) ||
+      cudaMemsetAsync(g->d_nrow, 0, g->nrow_bytes, c->stream) != cudaSuccess ||
+      cudaMemsetAsync(g->d_ncol, 0, g->ncol_bytes, c->stream) != cudaSuccess ||
+      cudaMemsetAsync(g->d_rtab, 0, g->rtab_bytes, c->stream) != cudaSuccess ||
+      cudaStreamSynchronize(c->stream) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return fail(CC_ERR_CUDA);
+  }
+  *out = g;
+  return CC_OK;
+}
+
+extern "C" void cc_graph_free(cc_graph* g) {
+  if (!g) return;
+  cc_context* c = g->ctx;
+  dev_free(c, g->d_row);
+  dev_free(c, g->d_col);
+  dev_free(c, g->d_perm);
+  dev_free(c, g->d_adj);
+  dev_free(c, g->d_rtab);
+  dev_free(c, g->d_nrow);
+  dev_free(c, g->d_ncol);
+  delete g;
+}
+
+extern "C" cc_status cc_graph_info(const cc_graph* g, uint32_t* n, uint64_t* m, uint32_t* max_degree) {
+  if (!g) return CC_ERR_ARG;
+  if (n) *n = g->n;
+  if (m) *m = g->m;
+  if (max_degree) *max_degree = g->maxdeg;
+  return CC_OK;
+}
+
+// ------------------------------------------------------------------ enumerate
+
+extern "C" cc_status cc_enumerate(cc_graph* g, uint32_t max_len, uint64_t* out_hist, uint64_t* out_hash,
+                                  uint64_t* out_tcount, cc_cycles* out_cycles, cc_run_info* out_info) {
+  if (!g || !out_hist || !out_hash) return CC_ERR_ARG;
+  if (out_cycles && ((out_cycles->capacity_cycles && !out_cycles->offsets) ||
+                     (out_cycles->capacity_vertices && !out_cycles->vertices)))
+    return CC_ERR_ARG;
+  cc_context* c = g->ctx;
+  const unsigned int n = g->n;
+  const unsigned int L = (max_len == 0 || max_len > n) ? n : max_len;
+  std::memset(out_hist, 0, sizeof(uint64_t) * (L + 1));
+  if (out_tcount) std::memset(out_tcount, 0, sizeof(uint64_t) * (L + 1));
+  *out_hash = 0;
+  cc_run_info info{};
+  if (out_cycles) out_cycles->count = out_cycles->total_vertices = 0;
+
+  // path choice: the bitset path needs n <= 256; the cycle list needs ordered paths (CSR)
+  Kind kind;
+  const unsigned int mode = c->opts.mode;
+  if (mode == CC_MODE_BITSET && (g->W == 0 || out_cycles)) return CC_ERR_UNSUPPORTED;
+  if (out_cycles || mode == CC_MODE_CSR || g->W == 0) kind = Kind::Csr;
+  else kind = g->W == 1 ? Kind::Bitset1 : (g->W == 2 ? Kind::Bitset2 : Kind::Bitset4);
+  info.mode = kind == Kind::Csr ? CC_MODE_CSR : CC_MODE_BITSET;
+  if (n < 3 || L < 3) {
+    if (out_info) *out_info = info;
+    c->last = info;
+    return CC_OK;
+  }
+  cc_status s;
+  if ((s = ensure_arena(c))) return s;
+  if ((s = ensure_frames(c, L + 4))) return s;
+  const size_t words = 2ull * (L + 1) + 2;
+  if ((s = ensure_results(c, words))) return s;
+  unsigned long long* d_hist = c->d_res;
+  unsigned long long* d_tcount = c->d_res + (L + 1);
+  unsigned long long* d_hash = c->d_res + 2 * (L + 1);
+
+  // optional cycle list buffers
+  unsigned int* d_cv = nullptr;
+  unsigned long long* d_cs = nullptr;
+  unsigned int* d_cl = nullptr;
+  const unsigned long long capc = out_cycles ? out_cycles->capacity_cycles : 0;
+  const unsigned long long capv = out_cycles ? out_cycles->capacity_vertices : 0;
+  auto free_cyc = [&]() {
+    dev_free(c, d_cv);
+    dev_free(c, d_cs);
+    dev_free(c, d_cl);
+  };
+  if (out_cycles) {
+    if ((s = dev_alloc(c, (void**)&d_cv, 4 * std::max(capv, 1ull))) ||
+        (s = dev_alloc(c, (void**)&d_cs, 8 * std::max(capc, 1ull))) ||
+        (s = dev_alloc(c, (void**)&d_cl, 4 * std::max(capc, 1ull)))) {
+      free_cyc();
+      return s;
+    }
+  }
+
+  const int W = kind == Kind::Bitset1 ? 1 : (kind == Kind::Bitset2 ? 2 : (kind == Kind::Bitset4 ? 4 : 0));
+  EngineParams p{};
+  p.arena = c->arena;
+  p.arena_bytes = c->arena_bytes;
+  p.ctl = c->ctl;
+  p.frames = c->frames;
+  p.max_depth = c->frames_cap;
+  p.n = n;
+  p.L = L;
+  p.maxch = std::max(1u, g->maxdeg > 0 ? g->maxdeg - 1 : 1u);
+  p.adj = g->d_adj;
+  p.rtab = g->d_rtab;
+  p.nrow = g->d_nrow;
+  p.ncol = g->d_ncol;
+  p.perm = g->d_perm;
+  p.hist = d_hist;
+  p.hash = d_hash;
+  p.tcount = d_tcount;
+  p.spin_limit = c->opts.spin_limit ? c->opts.spin_limit : kDefaultSpin;
+  p.fresh = 1;
+  p.seed_entries = (unsigned int)(2 * g->m);
+  p.cyc_vert = d_cv;
+  p.cyc_start = d_cs;
+  p.cyc_len = d_cl;
+  p.cyc_cap_c = capc;
+  p.cyc_cap_v = capv;
+  // frame 0 (initial triplets) sized by |T(G)| <= (Delta - 1) m / 2 (Section 2)
+  unsigned long long tb = g->maxdeg > 1 ? (unsigned long long)(g->maxdeg - 1) * g->m / 2 + 8 : 8;
+  const unsigned long long seed_stride = round_up(tb, 8);
+  const unsigned long long seed_bytes =
+      kind == Kind::Csr ? csr_region_bytes(seed_stride, 3) : bitset_region_bytes(seed_stride, W);
+  if (seed_bytes > c->arena_bytes / 2) {
+    free_cyc();
+    return CC_ERR_CAPACITY;
+  }
+  p.seed_stride = seed_stride;
+  p.seed_bytes = seed_bytes;
+  // graph staging into shared memory
+  size_t smem = 0;
+  if (kind == Kind::Csr) {
+    const size_t need = g->nrow_bytes + g->ncol_bytes + g->rtab_bytes;
+    if (need <= 160 * 1024) {
+      p.smem_graph = 1;
+      p.row_bytes = (unsigned int)g->nrow_bytes;
+      p.adj_bytes = (unsigned int)(g->nrow_bytes + g->ncol_bytes);
+      p.rtab_bytes = (unsigned int)g->rtab_bytes;
+      smem = need;
+    }
+  } else {
+    p.smem_graph = 1;
+    p.adj_bytes = (unsigned int)g->adj_bytes;
+    p.rtab_bytes = (unsigned int)g->rtab_bytes;
+    smem = g->adj_bytes + g->rtab_bytes;
+  }
+  const int block = c->opts.threads_per_block ? (int)c->opts.threads_per_block : 512;
+  const int grid = engine_grid(c, kind, block, smem);
+  if (grid <= 0) {
+    free_cyc();
+    return CC_ERR_CUDA;
+  }
+  info.grid_blocks = grid;
+
+  cudaStream_t st = c->stream;
+  cudaError_t e = cudaSuccess;
+  auto ok = [&](cudaError_t x) {
+    if (e == cudaSuccess && x != cudaSuccess) e = x;
+    return e == cudaSuccess;
+  };
+  ok(cudaEventRecord(c->ev0, st));
+  ok(cudaMemsetAsync(c->ctl, 0, sizeof(Control), st));
+  ok(cudaMemsetAsync(c->d_res, 0, words * 8, st));
+  ok(launch_label_single(g->d_row, g->d_col, n, W, g->d_perm, g->d_adj, g->d_rtab, g->d_nrow, g->d_ncol, st));
+  ok(launch_seed_single(kind, p, seed_stride, st));
+  ok(cudaEventRecord(c->ev3, st));
+  ok(launch_engine(kind, p, grid, block, smem, st));
+  ok(cudaEventRecord(c->ev1, st));
+  ok(cudaMemcpyAsync(c->h_res, c->d_res, words * 8, cudaMemcpyDeviceToHost, st));
+  ok(cudaMemcpyAsync(c->h_ctl, c->ctl, sizeof(Control), cudaMemcpyDeviceToHost, st));
+  ok(cudaEventRecord(c->ev2, st));
+  ok(cudaStreamSynchronize(st));
+  if (e != cudaSuccess) {
+    (void)cudaGetLastError();
+    free_cyc();
+    return cuda_status(e);
+  }
+  float ms1 = 0, ms2 = 0, ms3 = 0;
+  cudaEventElapsedTime(&ms1, c->ev0, c->ev1);
+  cudaEventElapsedTime(&ms2, c->ev0, c->ev2);
+  cudaEventElapsedTime(&ms3, c->ev3, c->ev1);
+  info.ms_engine = ms3;
+  const Control& h = *c->h_ctl;
+  s = map_dev_err(h.err);
+  std::memcpy(out_hist, c->h_res, sizeof(uint64_t) * (L + 1));
+  if (out_tcount) std::memcpy(out_tcount, c->h_res + (L + 1), sizeof(uint64_t) * (L + 1));
+  *out_hash = c->h_res[2 * (L + 1)];
+  info.ms_proc = ms1;
+  info.ms_total = ms2;
+  info.steps = h.step;
+  info.spilled = h.spilled;
+  info.peak_bytes = h.peak;
+  for (unsigned int k = 0; k <= L; ++k) {
+    info.cycles += c->h_res[k];
+    info.paths += c->h_res[L + 1 + k];
+  }
+  if (s == CC_OK && out_cycles) {
+    out_cycles->count = h.cyc_count;
+    out_cycles->total_vertices = h.cyc_verts;
+    if (h.cyc_count > capc || h.cyc_verts > capv) {
+      s = CC_ERR_TRUNCATED;
+    } else if (h.cyc_count) {
+      std::vector<uint32_t> hv(h.cyc_verts);
+      std::vector<unsigned long long> hs(h.cyc_count);
+      std::vector<uint32_t> hl(h.cyc_count);
+      if (cudaMemcpyAsync(hv.data(), d_cv, 4 * h.cyc_verts, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+          cudaMemcpyAsync(hs.data(), d_cs, 8 * h.cyc_count, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+          cudaMemcpyAsync(hl.data(), d_cl, 4 * h.cyc_count, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+          cudaStreamSynchronize(st) != cudaSuccess) {
+        (void)cudaGetLastError();
+        s = CC_ERR_CUDA;
+      } else {
+        uint64_t o = 0;
+        out_cycles->offsets[0] = 0;
+        for (unsigned long long i = 0; i < h.cyc_count; ++i) {
+          std::memcpy(out_cycles->vertices + o, hv.data() + hs[i], 4ull * hl[i]);
+          o += hl[i];
+          out_cycles->offsets[i + 1] = o;
+        }
+      }
+    } else if (capc) {
+      out_cycles->offsets[0] = 0;
+    }
+  }
+  free_cyc();
+  c->last = info;
+  if (out_info) *out_info = info;
+  return s;
+}
+
+// ------------------------------------------------------------------ batch
+
+extern "C" cc_status cc_batch_submit(cc_context* c, uint32_t count, const uint32_t* n, const uint64_t* row_off,
+                                     const uint32_t* row_ptr, const uint64_t* col_off, const uint32_t* col_idx,
+                                     uint32_t max_len, cc_batch_id* out) {
+  if (!c || !out || !n || !row_off || !row_ptr || !col_off) return CC_ERR_ARG;
+  if (c->batch.active) return CC_ERR_ARG;
+  if (count == 0 || count > kMultiMaxSlots) return count ? CC_ERR_UNSUPPORTED : CC_ERR_ARG;
+  auto& b = c->batch;
+  // validate every graph and build the packed, sorted copy
+  std::vector<uint32_t> rows, cols;
+  std::vector<unsigned long long> roff(count + 1), coff(count + 1);
+  std::vector<unsigned int> L(count);
+  unsigned long long tb_total = 0;
+  unsigned int maxch = 1;
+  std::vector<uint32_t> sorted;
+  for (uint32_t g = 0; g < count; ++g) {
+    if (n[g] > kMultiMaxN) {
+      *out = g;
+      return CC_ERR_UNSUPPORTED;
+    }
+    const uint32_t* rp = row_ptr + row_off[g];
+    unsigned int md = 0;
+    cc_status s = validate_csr(n[g], rp, col_idx ? col_idx + col_off[g] : nullptr, sorted, &md);
+    if (s) {
+      *out = g;
+      return s;
+    }
+    roff[g] = rows.size();
+    coff[g] = cols.size();
+    rows.insert(rows.end(), rp, rp + n[g] + 1);
+    cols.insert(cols.end(), sorted.begin(), sorted.end());
+    L[g] = (max_len == 0 || max_len > n[g]) ? n[g] : max_len;
+    const unsigned long long m = rp[n[g]] / 2;
+    if (md > 1) tb_total += (unsigned long long)(md - 1) * m / 2;
+    maxch = std::max(maxch, md > 1 ? md - 1 : 1u);
+  }
+  roff[count] = rows.size();
+  coff[count] = cols.size();
+  cc_status s;
+  if ((s = ensure_arena(c))) return s;
+  if ((s = ensure_frames(c, 70))) return s;
+  // device pack: rows | cols | roff | coff | n | adj | rtab | Lg | hist | hash | tcount | last | ts
+  b.ts_cap = 1u << 16;
+  auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
+  size_t off = 0;
+  const size_t o_rows = off; off = al(off + 4 * rows.size());
+  const size_t o_cols = off; off = al(off + 4 * std::max<size_t>(cols.size(), 1));
+  const size_t o_roff = off; off = al(off + 8 * (count + 1));
+  const size_t o_coff = off; off = al(off + 8 * (count + 1));
+  const size_t o_n = off; off = al(off + 4 * count);
+  const size_t o_adj = off; off = al(off + 8ull * 64 * count);
+  const size_t o_rtab = off; off = al(off + 8ull * 64 * count);
+  const size_t o_Lg = off; off = al(off + count);
+  const size_t o_hist = off; off = al(off + 8ull * kMultiHistStride * count);
+  const size_t o_hash = off; off = al(off + 8ull * count);
+  const size_t o_tc = off; off = al(off + 8ull * kMultiHistStride * count);
+  const size_t o_last = off; off = al(off + 4ull * count);
+  const size_t o_ts = off; off = al(off + 8ull * b.ts_cap);
+  const size_t total = off;
+  if (b.d_pack_bytes < total) {
+    dev_free(c, b.d_pack);
+    b.d_pack = nullptr;
+    b.d_pack_bytes = 0;
+    if ((s = dev_alloc(c, &b.d_pack, total))) return s;
+    b.d_pack_bytes = total;
+  }
+  unsigned char* base = static_cast<unsigned char*>(b.d_pack);
+  cudaStream_t st = c->stream;
+  cudaError_t e = cudaSuccess;
+  auto ok = [&](cudaError_t x) {
+    if (e == cudaSuccess && x != cudaSuccess) e = x;
+  };
+  std::vector<unsigned int> nv(n, n + count);
+  ok(cudaEventRecord(c->ev0, st));
+  ok(cudaMemcpyAsync(base + o_rows, rows.data(), 4 * rows.size(), cudaMemcpyHostToDevice, st));
+  if (!cols.empty()) ok(cudaMemcpyAsync(base + o_cols, cols.data(), 4 * cols.size(), cudaMemcpyHostToDevice, st));
+  ok(cudaMemcpyAsync(base + o_roff, roff.data(), 8 * (count + 1), cudaMemcpyHostToDevice, st));
+  ok(cudaMemcpyAsync(base + o_coff, coff.data(), 8 * (count + 1), cudaMemcpyHostToDevice, st));
+  ok(cudaMemcpyAsync(base + o_n, nv.data(), 4 * count, cudaMemcpyHostToDevice, st));
+  ok(cudaMemsetAsync(base + o_hist, 0, o_ts - o_hist, st));
+  ok(cudaMemsetAsync(c->ctl, 0, sizeof(Control), st));
+  // synchronise so the host copies can be released when this call returns
+  ok(cudaStreamSynchronize(st));
+  if (e != cudaSuccess) {
+    (void)cudaGetLastError();
+    return cuda_status(e);
+  }
+  EngineParams p{};
+  p.arena = c->arena;
+  p.arena_bytes = c->arena_bytes;
+  p.ctl = c->ctl;
+  p.frames = c->frames;
+  p.max_depth = c->frames_cap;
+  p.n = 64;
+  p.L = 64;
+  p.maxch = maxch;
+  p.adj = reinterpret_cast<unsigned long long*>(base + o_adj);
+  p.rtab = reinterpret_cast<unsigned long long*>(base + o_rtab);
+  p.Lg = base + o_Lg;
+  p.hist = reinterpret_cast<unsigned long long*>(base + o_hist);
+  p.hash = reinterpret_cast<unsigned long long*>(base + o_hash);
+  p.tcount = reinterpret_cast<unsigned long long*>(base + o_tc);
+  p.last_step = reinterpret_cast<unsigned int*>(base + o_last);
+  p.step_ts = reinterpret_cast<unsigned long long*>(base + o_ts);
+  p.step_ts_cap = b.ts_cap;
+  p.spin_limit = c->opts.spin_limit ? c->opts.spin_limit : kDefaultSpin;
+  p.fresh = 1;
+  const unsigned long long seed_stride = round_up(tb_total + 8, 8);
+  const unsigned long long seed_bytes = bitset_region_bytes(seed_stride, 1);
+  if (seed_bytes > c->arena_bytes / 2) return CC_ERR_CAPACITY;
+  p.seed_stride = seed_stride;
+  p.seed_bytes = seed_bytes;
+  const int block = c->opts.threads_per_block ? (int)c->opts.threads_per_block : 512;
+  const int grid = engine_grid(c, Kind::Multi, block, 0);
+  if (grid <= 0) return CC_ERR_CUDA;
+  ok(launch_label_seed_multi(reinterpret_cast<unsigned int*>(base + o_rows),
+                             reinterpret_cast<unsigned long long*>(base + o_roff),
+                             reinterpret_cast<unsigned int*>(base + o_cols),
+                             reinterpret_cast<unsigned long long*>(base + o_coff),
+                             reinterpret_cast<unsigned int*>(base + o_n), count, 0, max_len, p, 0, seed_stride,
+                             &c->ctl->seed_count, &c->ctl->seed_next, st));
+  ok(cudaEventRecord(c->ev1, st));
+  ok(launch_engine(Kind::Multi, p, grid, block, 0, st));
+  ok(cudaEventRecord(c->ev2, st));
+  if (e != cudaSuccess) {
+    (void)cudaGetLastError();
+    return cuda_status(e);
+  }
+  b.active = true;
+  b.count = count;
+  b.max_len = max_len;
+  b.L = L;
+  b.d_hist = p.hist;
+  b.d_hash = p.hash;
+  b.d_tcount = p.tcount;
+  b.d_last = p.last_step;
+  b.d_ts = p.step_ts;
+  b.grid = grid;
+  b.id = c->next_batch++;
+  *out = b.id;
+  return CC_OK;
+}
+
+extern "C" cc_status cc_batch_poll(cc_context* c, cc_batch_id id, uint32_t timeout_us, uint64_t* hist,
+                                   uint32_t hist_stride, uint64_t* hash, uint64_t* paths, double* done_us,
+                                   cc_run_info* info) {
+  if (!c || !hist || !hash || hist_stride == 0) return CC_ERR_ARG;
+  auto& b = c->batch;
+  if (!b.active || b.id != id) return CC_ERR_ARG;
+  const auto t0 = std::chrono::steady_clock::now();
+  for (;;) {
+    cudaError_t q = cudaEventQuery(c->ev2);
+    if (q == cudaSuccess) break;
+    if (q != cudaErrorNotReady) {
+      (void)cudaGetLastError();
+      b.active = false;
+      return CC_ERR_CUDA;
+    }
+    const auto el = std::chrono::duration_cast<std::chrono::microseconds>(std::chrono::steady_clock::now() - t0);
+    if ((uint64_t)el.count() >= timeout_us) return CC_PENDING;
+    std::this_thread::sleep_for(std::chrono::microseconds(20));
+  }
+  const unsigned int count = b.count;
+  std::vector<unsigned long long> hh(kMultiHistStride * (size_t)count), ht(kMultiHistStride * (size_t)count),
+      hs(count), ts;
+  std::vector<unsigned int> hl(count);
+  cudaStream_t st = c->stream;
+  cudaError_t e = cudaSuccess;
+  auto ok = [&](cudaError_t x) {
+    if (e == cudaSuccess && x != cudaSuccess) e = x;
+  };
+  ok(cudaMemcpyAsync(hh.data(), b.d_hist, 8 * hh.size(), cudaMemcpyDeviceToHost, st));
+  ok(cudaMemcpyAsync(ht.data(), b.d_tcount, 8 * ht.size(), cudaMemcpyDeviceToHost, st));
+  ok(cudaMemcpyAsync(hs.data(), b.d_hash, 8 * count, cudaMemcpyDeviceToHost, st));
+  ok(cudaMemcpyAsync(hl.data(), b.d_last, 4 * count, cudaMemcpyDeviceToHost, st));
+  ok(cudaMemcpyAsync(c->h_ctl, c->ctl, sizeof(Control), cudaMemcpyDeviceToHost, st));
+  ok(cudaStreamSynchronize(st));
+  if (e != cudaSuccess) {
+    (void)cudaGetLastError();
+    b.active = false;
+    return CC_ERR_CUDA;
+  }
+  const Control& h = *c->h_ctl;
+  const unsigned long long nsteps = h.step;
+  ts.resize(std::min<unsigned long long>(nsteps, b.ts_cap));
+  if (!ts.empty()) {
+    ok(cudaMemcpyAsync(ts.data(), b.d_ts, 8 * ts.size(), cudaMemcpyDeviceToHost, st));
+    ok(cudaStreamSynchronize(st));
+  }
+  b.active = false;
+  cc_status s = map_dev_err(h.err);
+  float ms_seed = 0, ms_all = 0;
+  cudaEventElapsedTime(&ms_seed, c->ev0, c->ev1);
+  cudaEventElapsedTime(&ms_all, c->ev0, c->ev2);
+  cc_run_info ri{};
+  float ms_eng = 0;
+  cudaEventElapsedTime(&ms_eng, c->ev1, c->ev2);
+  ri.ms_proc = ms_all;
+  ri.ms_total = ms_all;
+  ri.ms_engine = ms_eng;
+  ri.steps = nsteps;
+  ri.spilled = h.spilled;
+  ri.peak_bytes = h.peak;
+  ri.mode = CC_MODE_BITSET;
+  ri.grid_blocks = b.grid;
+  // step timestamps are absolute (globaltimer), measured from the engine's start
+  const double t_start_ns = (double)h.t_start;
+  for (unsigned int g = 0; g < count; ++g) {
+    const unsigned int Lg = b.L[g];
+    for (unsigned int k = 0; k < hist_stride; ++k)
+      hist[(size_t)g * hist_stride + k] = (k <= Lg && k < (unsigned)kMultiHistStride) ? hh[(size_t)g * kMultiHistStride + k] : 0;
+    hash[g] = hs[g];
+    unsigned long long pg = 0, cg = 0;
+    for (int k = 0; k < kMultiHistStride; ++k) {
+      pg += ht[(size_t)g * kMultiHistStride + k];
+      cg += hh[(size_t)g * kMultiHistStride + k];
+    }
+    if (paths) paths[g] = pg;
+    ri.paths += pg;
+    ri.cycles += cg;
+    if (done_us) {
+      // a graph is finished at the end of the last step that expanded one of its paths
+      // (graphs with no stored path finish with seeding: 0)
+      const unsigned int ls = hl[g];
+      const bool expanded = ht[(size_t)g * kMultiHistStride + 3] != 0;
+      done_us[g] = (expanded && ls < ts.size()) ? ((double)ts[ls] - t_start_ns) / 1000.0 : 0.0;
+    }
+  }
+  if (info) *info = ri;
+  c->last = ri;
+  return s;
+}

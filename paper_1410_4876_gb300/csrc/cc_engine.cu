@@ -1,0 +1,678 @@
+// Persistent expansion engine: Algorithm 3 (ExpandingChordlessPathsParallel) executed
+// level after level inside ONE cooperative launch, replacing the host relaunch loop of
+// Algorithm 4 by grid-wide barriers (Section 4.4 uses persistent threads within a level;
+// here the persistence also spans the levels).
+//
+// Control.  Every block keeps an identical copy of the frame chain's top in shared
+// memory and applies the same deterministic plan/commit rules, so the only grid-wide
+// communication per step is the child counters read after the barrier.  Block 0 also
+// mirrors frames into global memory so any block can pop back to them.
+//
+// Per step: take the top frame, choose how much of it to expand (all of it if the exact
+// or bounded child count fits the free arena, else the largest chunk that fits; that
+// chunk's subtree then runs depth-first), expand those paths with one thread per path,
+// compact the children with a block scan and one atomic per tile, accumulate cycles.
+#include "cc_internal.cuh"
+
+namespace cc {
+
+constexpr int kMaxThreads = 512;
+
+struct StepPlan {
+  unsigned long long src_base, src_stride, begin, end;
+  unsigned long long dst_base, dst_stride;
+  unsigned long long s;
+  unsigned int t;
+  unsigned int done;
+};
+
+struct LocalState {
+  Frame cur;
+  Frame child;
+  unsigned long long bot, top, chunk;
+  unsigned int depth, has_child;
+};
+
+__device__ __forceinline__ Frame load_frame(const Frame* f) {
+  Frame r;
+  const unsigned long long* q = reinterpret_cast<const unsigned long long*>(f);
+  r.base = __ldcg(q + 0);
+  r.bytes = __ldcg(q + 1);
+  r.stride = __ldcg(q + 2);
+  r.count = __ldcg(q + 3);
+  r.cursor = __ldcg(q + 4);
+  r.next = __ldcg(q + 5);
+  const unsigned long long te = __ldcg(q + 6);
+  r.t = (unsigned int)(te & 0xFFFFFFFFull);
+  r.end = (unsigned int)(te >> 32);
+  return r;
+}
+__device__ __forceinline__ void store_frame(Frame* f, const Frame& r) { *f = r; }
+
+template <Kind K>
+struct KindTraits {
+  static constexpr int W = K == Kind::Bitset2 ? 2 : (K == Kind::Bitset4 ? 4 : 1);
+  static constexpr bool multi = K == Kind::Multi;
+  static constexpr bool csr = K == Kind::Csr;
+  static constexpr int P = K == Kind::Bitset4 ? 1 : 2;  // paths per thread per tile
+};
+
+template <Kind K>
+__device__ __forceinline__ unsigned long long region_bytes(unsigned long long stride, unsigned int t_child) {
+  if constexpr (KindTraits<K>::csr) return csr_region_bytes(stride, t_child);
+  else return bitset_region_bytes(stride, KindTraits<K>::W);
+}
+template <Kind K>
+__device__ __forceinline__ unsigned long long record_bytes(unsigned int t_child) {
+  if constexpr (KindTraits<K>::csr) return 2ull * t_child;
+  else return 8ull * KindTraits<K>::W + 12ull;
+}
+
+// ------------------------------------------------------------------ control (thread 0)
+
+template <Kind K>
+__device__ bool plan_step(const EngineParams& p, LocalState& st, StepPlan& pl) {
+  while (st.depth > 0 && st.cur.cursor >= st.cur.count) {  // pop finished frames
+    if (st.cur.end == 0) st.bot = st.cur.base; else st.top = st.cur.base + st.cur.bytes;
+    st.depth -= 1;
+    if (st.depth > 0) st.cur = load_frame(&p.frames[st.depth - 1]);
+  }
+  if (st.depth == 0) return false;
+  const Frame& f = st.cur;
+  const unsigned long long rem = f.count - f.cursor;
+  const unsigned int t = f.t;
+  unsigned long long need;
+  if constexpr (KindTraits<K>::csr) {
+    need = (t + 1 < p.L) ? rem * p.maxch : 0ull;
+  } else if constexpr (KindTraits<K>::multi) {
+    need = (f.cursor == 0 && f.next != kNoNext) ? f.next : rem * p.maxch;
+  } else {
+    need = (t + 1 >= p.L) ? 0ull : ((f.cursor == 0 && f.next != kNoNext) ? f.next : rem * p.maxch);
+  }
+  const unsigned long long res = KindTraits<K>::multi ? p.reserve : 0ull;
+  unsigned long long cap = need + (need || res ? res : 0ull);
+  st.chunk = rem;
+  st.has_child = 0;
+  if (cap > 0) {
+    const unsigned long long rb = record_bytes<K>(t + 1);
+    const unsigned long long freeb = st.top - st.bot;
+    const unsigned long long maxcap = freeb > 1024 ? ((freeb - 1024) / rb) & ~7ull : 0ull;
+    if (cap > maxcap) {
+      // Spill: this chunk's subtree runs depth-first before the rest of the frame, and
+      // each deeper stored level of that subtree needs room too, so the chunk's children
+      // get only an equal share of the free space among those levels.
+      const unsigned long long levels =
+          KindTraits<K>::multi ? (st.depth + 4 < p.L ? p.L - 3ull - st.depth : 1ull)
+                               : (p.L > t + 2 ? (unsigned long long)(p.L - t - 1) : 1ull);
+      const unsigned long long share = maxcap / levels;
+      unsigned long long ch = share > res ? (share - res) / p.maxch : 0ull;
+      if (ch == 0 && maxcap >= res + p.maxch) ch = 1;
+      if (ch == 0) {
+        set_err(p.ctl, kDevCapacity, (int)t);
+        return false;
+      }
+      if (ch < rem) {
+        st.chunk = ch;
+        if (blockIdx.x == 0) p.ctl->spilled = 1;
+      }
+      cap = st.chunk * p.maxch + res;
+    }
+    const unsigned long long stride = round_up(cap, 8);
+    const unsigned long long bytes = region_bytes<K>(stride, t + 1);
+    Frame& c = st.child;
+    c.end = 1u - f.end;
+    c.base = c.end ? st.top - bytes : st.bot;
+    c.bytes = bytes;
+    c.stride = stride;
+    c.count = 0;
+    c.cursor = 0;
+    c.next = kNoNext;
+    c.t = KindTraits<K>::multi ? 0u : t + 1;
+    st.has_child = 1;
+    if (blockIdx.x == 0) {
+      const unsigned long long used = p.arena_bytes - (freeb - bytes);
+      if (used > p.ctl->peak) p.ctl->peak = used;
+    }
+  }
+  pl.src_base = f.base;
+  pl.src_stride = f.stride;
+  pl.begin = f.cursor;
+  pl.end = f.cursor + st.chunk;
+  pl.dst_base = st.has_child ? st.child.base : 0ull;
+  pl.dst_stride = st.has_child ? st.child.stride : 0ull;
+  pl.t = t;
+  return true;
+}
+
+template <Kind K>
+__device__ void commit_step(const EngineParams& p, LocalState& st, unsigned long long c, unsigned long long nx,
+                            bool writer) {
+  const unsigned int t = st.cur.t;
+  st.cur.cursor += st.chunk;
+  const bool consumed = st.cur.cursor >= st.cur.count;
+  if (consumed) {
+    if (st.cur.end == 0) st.bot = st.cur.base; else st.top = st.cur.base + st.cur.bytes;
+    st.depth -= 1;
+  } else if (writer) {
+    store_frame(&p.frames[st.depth - 1], st.cur);
+  }
+  if (st.has_child && c > 0) {
+    Frame g = st.child;
+    g.count = c;
+    g.cursor = 0;
+    g.next = KindTraits<K>::csr ? kNoNext : nx;
+    if (g.end) st.top = g.base; else st.bot = g.base + g.bytes;
+    if (st.depth >= p.max_depth) {
+      set_err(p.ctl, kDevDepth, (int)st.depth);
+      return;
+    }
+    if (writer) {
+      store_frame(&p.frames[st.depth], g);
+      if constexpr (!KindTraits<K>::multi) atomicAdd(&p.tcount[t + 1], c);
+    }
+    st.depth += 1;
+    st.cur = g;
+  } else if (consumed && st.depth > 0) {
+    st.cur = load_frame(&p.frames[st.depth - 1]);
+  }
+}
+
+// ------------------------------------------------------------------ bitset expansion
+
+// Algorithm 3 on bitset records.  For a path p = <v1 .. vt> with blocked set B:
+//   cand  = Adj(vt) & ~B      label test (l(v) > l(v2)), v not on p, chord test v2..v_{t-1}
+//   close = cand & Adj(v1)    chordless cycles <p, v> of t+1 vertices
+//   child = cand & ~Adj(v1)   chordless paths <p, v>, blocked set B | Adj(vt)
+// The exact child count of each new path is popc(Adj(v) & ~(B | Adj(vt)) & ~Adj(v1)),
+// summed so the next frame's size is known before it is expanded.
+template <Kind K>
+__device__ __forceinline__ void process_bitset(const EngineParams& p, const StepPlan& pl,
+                                               const unsigned long long* adj, const unsigned long long* rtab,
+                                               unsigned int* s_warp, unsigned long long* s_red,
+                                               unsigned long long* s_base) {
+  constexpr int W = KindTraits<K>::W;
+  constexpr int P = KindTraits<K>::P;
+  constexpr bool MULTI = KindTraits<K>::multi;
+  const unsigned int tid = threadIdx.x, lane = tid & 31;
+  const unsigned long long ss = pl.src_stride, ds = pl.dst_stride;
+  const unsigned long long* sB = reinterpret_cast<const unsigned long long*>(p.arena + pl.src_base);
+  const unsigned long long* sH = sB + W * ss;
+  const unsigned int* sM = reinterpret_cast<const unsigned int*>(sH + ss);
+  unsigned long long* dB = reinterpret_cast<unsigned long long*>(p.arena + pl.dst_base);
+  unsigned long long* dH = dB + W * ds;
+  unsigned int* dM = reinterpret_cast<unsigned int*>(dH + ds);
+  const bool store = ds != 0;
+  const unsigned int t = pl.t, L = p.L;
+  const unsigned long long s = pl.s;
+  const bool close_ok1 = t + 1 <= L, next_ok1 = t + 2 < L;
+  unsigned long long nx = 0, ncyc = 0, hacc = 0;
+  const unsigned long long tile = (unsigned long long)P * blockDim.x;
+
+  for (unsigned long long t0 = pl.begin + (unsigned long long)blockIdx.x * tile; t0 < pl.end;
+       t0 += (unsigned long long)gridDim.x * tile) {
+    unsigned long long B[P][W], H[P], ch[P][W];
+    unsigned int M[P];
+    unsigned int nch = 0;
+    unsigned int mcyc[P], mch[P], mkey[P];
+    unsigned long long mh[P];
+#pragma unroll
+    for (int j = 0; j < P; ++j) {
+      const unsigned long long i = t0 + (unsigned long long)j * blockDim.x + tid;
+      const bool valid = i < pl.end;
+#pragma unroll
+      for (int k = 0; k < W; ++k) B[j][k] = valid ? ldcg64(sB + k * ss + i) : ~0ull;
+      H[j] = valid ? ldcg64(sH + i) : 0ull;
+      M[j] = valid ? ldcg32(sM + i) : 0u;
+      unsigned int v1, vt, tt = t, Lr = L;
+      unsigned long long go = 0;
+      if constexpr (MULTI) {
+        v1 = M[j] & 63u;
+        vt = (M[j] >> 6) & 63u;
+        tt = (M[j] >> 12) & 63u;
+        const unsigned int g = M[j] >> 18;
+        go = (unsigned long long)g * 64ull;
+        Lr = valid ? __ldg(p.Lg + g) : 0u;
+      } else {
+        v1 = M[j] & 0xFFFFu;
+        vt = M[j] >> 16;
+      }
+      const bool close_ok = MULTI ? (tt + 1 <= Lr) : close_ok1;
+      const bool store_ok = MULTI ? (store && tt + 1 < Lr) : store;
+      unsigned int cc = 0, nj = 0;
+      unsigned long long hh = 0;
+#pragma unroll
+      for (int k = 0; k < W; ++k) {
+        const unsigned long long at = MULTI ? __ldg(adj + go + vt) : adj[(unsigned long long)vt * W + k];
+        const unsigned long long a1 = MULTI ? __ldg(adj + go + v1) : adj[(unsigned long long)v1 * W + k];
+        const unsigned long long cand = at & ~B[j][k];
+        unsigned long long close = cand & a1;
+        ch[j][k] = store_ok ? (cand & ~a1) : 0ull;
+        nj += __popcll(ch[j][k]);
+        if (close_ok) {
+          cc += __popcll(close);
+          while (close) {
+            const unsigned int v = 64u * k + __ffsll((long long)close) - 1;
+            close &= close - 1;
+            const unsigned long long rv = MULTI ? __ldg(rtab + go + v) : rtab[v];
+            hh += mix64(H[j] + rv + (unsigned long long)(tt + 1) * kGamma);
+          }
+        }
+      }
+      nch += nj;
+      if constexpr (MULTI) {
+        mcyc[j] = cc;
+        mh[j] = hh;
+        mch[j] = nj;
+        mkey[j] = valid ? ((M[j] >> 18) << 6 | tt) : 0xFFFFFFFFu;
+      } else {
+        ncyc += cc;
+        hacc += hh;
+      }
+    }
+    if constexpr (MULTI) {
+      // per (slot, length) statistics, aggregated over the lanes of the warp that share them
+#pragma unroll
+      for (int j = 0; j < P; ++j) {
+        unsigned int pending = __ballot_sync(0xffffffffu, mkey[j] != 0xFFFFFFFFu);
+        while (pending) {
+          const int leader = __ffs(pending) - 1;
+          const unsigned int lk = __shfl_sync(0xffffffffu, mkey[j], leader);
+          const bool mine = mkey[j] == lk;
+          const unsigned int grp = __ballot_sync(0xffffffffu, mine);
+          const unsigned int c = __reduce_add_sync(0xffffffffu, mine ? mcyc[j] : 0u);
+          const unsigned int kk = __reduce_add_sync(0xffffffffu, mine ? mch[j] : 0u);
+          const unsigned long long h = warp_sum_u64(mine ? mh[j] : 0ull);
+          if ((int)lane == leader) {
+            const unsigned int g = lk >> 6, tt = lk & 63u;
+            const unsigned long long hb = (unsigned long long)g * kMultiHistStride;
+            if (c) atomicAdd(&p.hist[hb + tt + 1], (unsigned long long)c);
+            if (h) atomicAdd(&p.hash[g], h);
+            if (kk) atomicAdd(&p.tcount[hb + tt + 1], (unsigned long long)kk);
+            if (p.live) atomicAdd(reinterpret_cast<unsigned long long*>(&p.live[g]),
+                                  (unsigned long long)((long long)kk - (long long)__popc(grp)));
+            if (p.last_step) atomicMax(&p.last_step[g], (unsigned int)s);
+          }
+          pending &= ~grp;
+        }
+      }
+    }
+    if (store) {
+      unsigned int tot;
+      const unsigned int off = block_exclusive_scan(nch, &tot, s_warp);
+      if (tid == 0) *s_base = tot ? atomicAdd(&p.ctl->cnt[s % 3], (unsigned long long)tot) : 0ull;
+      __syncthreads();
+      if (tot) {
+        unsigned long long slot = *s_base + off;
+#pragma unroll
+        for (int j = 0; j < P; ++j) {
+          unsigned long long any = 0;
+#pragma unroll
+          for (int k = 0; k < W; ++k) any |= ch[j][k];
+          if (!any) continue;
+          unsigned int v1, vt, tt = t, Lr = L, mhi = 0;
+          unsigned long long go = 0;
+          if constexpr (MULTI) {
+            v1 = M[j] & 63u;
+            vt = (M[j] >> 6) & 63u;
+            tt = (M[j] >> 12) & 63u;
+            const unsigned int g = M[j] >> 18;
+            go = (unsigned long long)g * 64ull;
+            Lr = __ldg(p.Lg + g);
+            mhi = v1 | ((tt + 1) << 12) | (g << 18);
+          } else {
+            v1 = M[j] & 0xFFFFu;
+            vt = M[j] >> 16;
+            mhi = v1;
+          }
+          const bool next_ok = MULTI ? (tt + 2 < Lr) : next_ok1;
+          unsigned long long nb[W], a1[W];
+#pragma unroll
+          for (int k = 0; k < W; ++k) {
+            nb[k] = B[j][k] | (MULTI ? __ldg(adj + go + vt) : adj[(unsigned long long)vt * W + k]);
+            a1[k] = MULTI ? __ldg(adj + go + v1) : adj[(unsigned long long)v1 * W + k];
+          }
+#pragma unroll
+          for (int k = 0; k < W; ++k) {
+            unsigned long long b = ch[j][k];
+            while (b) {
+              const unsigned int v = 64u * k + __ffsll((long long)b) - 1;
+              b &= b - 1;
+              if (slot < ds) {
+#pragma unroll
+                for (int q = 0; q < W; ++q) dB[q * ds + slot] = nb[q];
+                dH[slot] = H[j] + (MULTI ? __ldg(rtab + go + v) : rtab[v]);
+                dM[slot] = MULTI ? (mhi | (v << 6)) : (mhi | (v << 16));
+                if (next_ok) {
+#pragma unroll
+                  for (int q = 0; q < W; ++q) {
+                    const unsigned long long av =
+                        MULTI ? __ldg(adj + go + v) : adj[(unsigned long long)v * W + q];
+                    nx += __popcll(av & ~nb[q] & ~a1[q]);
+                  }
+                }
+              } else {
+                set_err(p.ctl, kDevBounds, 1);
+              }
+              ++slot;
+            }
+          }
+        }
+      }
+    }
+  }
+  const unsigned long long rn = block_sum_u64(nx, s_red);
+  if (tid == 0 && rn) atomicAdd(&p.ctl->nxt[s % 3], rn);
+  if constexpr (!MULTI) {
+    const unsigned long long rc = block_sum_u64(ncyc, s_red);
+    if (tid == 0 && rc) atomicAdd(&p.hist[t + 1], rc);
+    const unsigned long long rh = block_sum_u64(hacc, s_red);
+    if (tid == 0 && rh) atomicAdd(p.hash, rh);
+  }
+}
+
+// ------------------------------------------------------------------ CSR expansion
+
+// Path held in registers as CAP u16 ids packed two per word (unused slots 0xFFFF, never
+// a vertex id).  CAP = 0: the path is re-read from its planes (long paths).
+template <int CAP>
+struct PathRegs {
+  static constexpr int NP = CAP > 0 ? CAP / 2 : 1;
+  unsigned int pk[NP];
+};
+
+template <int CAP>
+__device__ __forceinline__ bool on_path(const PathRegs<CAP>& r, unsigned int w, const unsigned short* S,
+                                        unsigned long long ss, unsigned long long i, unsigned int t) {
+  if constexpr (CAP > 0) {
+    const unsigned int ww = w | (w << 16);
+    unsigned int any = 0;
+#pragma unroll
+    for (int q = 0; q < PathRegs<CAP>::NP; ++q) {
+      const unsigned int x = r.pk[q] ^ ww;  // a zero 16-bit lane marks an equal id
+      any |= (x - 0x00010001u) & ~x & 0x80008000u;
+    }
+    return any != 0;
+  } else {
+    for (unsigned int k = 1; k + 1 < t; ++k)
+      if (ldcg16(S + k * ss + i) == w) return true;
+    return false;
+  }
+}
+
+// Algorithm 3 on CSR with the path as a vertex list.  Candidate v of Adj(vt):
+//   label test   v > v2 (relabelled ids are label ranks), v != v_{t-1} (the only vertex
+//                of a stored chordless path adjacent to vt);
+//   chord test   no w in Adj(v) lies on v2..v_{t-1} (a 64-bit signature of the interior
+//                filters most w before the exact comparison);
+//   close test   v1 in Adj(v) gives a cycle of t+1 vertices, otherwise a child path.
+template <int CAP>
+__device__ __forceinline__ void process_csr(const EngineParams& p, const StepPlan& pl, const unsigned int* nrow,
+                                            const unsigned short* ncol, const unsigned long long* rtab,
+                                            unsigned int* s_warp, unsigned long long* s_red,
+                                            unsigned long long* s_base) {
+  constexpr int NP = PathRegs<CAP>::NP;
+  const unsigned int tid = threadIdx.x;
+  const unsigned int t = pl.t, L = p.L;
+  const unsigned long long ss = pl.src_stride, ds = pl.dst_stride;
+  const unsigned short* S = reinterpret_cast<const unsigned short*>(p.arena + pl.src_base);
+  unsigned short* D = reinterpret_cast<unsigned short*>(p.arena + pl.dst_base);
+  const bool store = ds != 0;
+  const bool close_ok = t + 1 <= L;
+  const unsigned long long s = pl.s;
+  unsigned long long ncyc = 0, hacc = 0;
+  for (unsigned long long t0 = pl.begin + (unsigned long long)blockIdx.x * blockDim.x; t0 < pl.end;
+       t0 += (unsigned long long)gridDim.x * blockDim.x) {
+    const unsigned long long i = t0 + tid;
+    const bool valid = i < pl.end;
+    PathRegs<CAP> r;
+    unsigned int v1 = 0xFFFFu, v2 = 0xFFFFu, vt = 0, vp = 0, rb = 0, deg = 0;
+    unsigned long long sig = 0;
+    if (valid) {
+      if constexpr (CAP > 0) {
+#pragma unroll
+        for (int q = 0; q < NP; ++q) {
+          const unsigned int lo = (2u * q < t) ? ldcg16(S + (2ull * q) * ss + i) : 0xFFFFu;
+          const unsigned int hi = (2u * q + 1 < t) ? ldcg16(S + (2ull * q + 1) * ss + i) : 0xFFFFu;
+          r.pk[q] = lo | (hi << 16);
+          if (2u * q >= 1 && 2u * q + 2 <= t) sig |= 1ull << (lo & 63u);
+          if (2u * q + 1 >= 1 && 2u * q + 3 <= t) sig |= 1ull << (hi & 63u);
+        }
+        v1 = r.pk[0] & 0xFFFFu;
+        v2 = r.pk[0] >> 16;
+      } else {
+        r.pk[0] = 0;
+        v1 = ldcg16(S + i);
+        v2 = ldcg16(S + ss + i);
+        for (unsigned int k = 1; k + 1 < t; ++k) sig |= 1ull << (ldcg16(S + k * ss + i) & 63u);
+      }
+      vt = ldcg16(S + (unsigned long long)(t - 1) * ss + i);
+      vp = ldcg16(S + (unsigned long long)(t - 2) * ss + i);
+      rb = nrow[vt];
+      deg = nrow[vt + 1] - rb;
+    }
+    for (unsigned int w0 = 0; __syncthreads_or(valid && w0 < deg); w0 += 32) {
+      unsigned int mask = 0;
+      if (valid && w0 < deg) {
+        const unsigned int qend = min(deg, w0 + 32);
+        for (unsigned int q = w0; q < qend; ++q) {
+          const unsigned int v = ncol[rb + q];
+          if (v <= v2 || v == vp) continue;
+          bool close = false, chord = false;
+          const unsigned int e1 = nrow[v + 1];
+          for (unsigned int e = nrow[v]; e < e1; ++e) {
+            const unsigned int w = ncol[e];
+            if (w < v2 || w == vt) continue;
+            if (w == v1) { close = true; continue; }
+            if (((sig >> (w & 63u)) & 1ull) && on_path<CAP>(r, w, S, ss, i, t)) { chord = true; break; }
+          }
+          if (chord) continue;
+          if (close) {
+            if (close_ok) {
+              ++ncyc;
+              unsigned long long hs = rtab[v];
+              if constexpr (CAP > 0) {
+#pragma unroll
+                for (int q = 0; q < NP; ++q) {
+                  if (2u * q < t) hs += rtab[r.pk[q] & 0xFFFFu];
+                  if (2u * q + 1 < t) hs += rtab[r.pk[q] >> 16];
+                }
+              } else {
+                for (unsigned int k = 0; k < t; ++k) hs += rtab[ldcg16(S + k * ss + i)];
+              }
+              hacc += mix64(hs + (unsigned long long)(t + 1) * kGamma);
+              if (p.cyc_vert)
+                emit_cycle(p, t + 1, [&](unsigned int j) -> unsigned int {
+                  return j < t ? (unsigned int)ldcg16(S + (unsigned long long)j * ss + i) : v;
+                });
+            }
+          } else if (store) {
+            mask |= 1u << (q - w0);
+          }
+        }
+      }
+      if (store) {
+        unsigned int tot;
+        const unsigned int off = block_exclusive_scan(__popc(mask), &tot, s_warp);
+        if (tid == 0) *s_base = tot ? atomicAdd(&p.ctl->cnt[s % 3], (unsigned long long)tot) : 0ull;
+        __syncthreads();
+        if (tot) {
+          unsigned long long slot = *s_base + off;
+          while (mask) {
+            const unsigned int q = __ffs(mask) - 1;
+            mask &= mask - 1;
+            const unsigned int v = ncol[rb + w0 + q];
+            if (slot < ds) {
+              if constexpr (CAP > 0) {
+#pragma unroll
+                for (int qq = 0; qq < NP; ++qq) {
+                  if (2u * qq < t) D[(2ull * qq) * ds + slot] = (unsigned short)(r.pk[qq] & 0xFFFFu);
+                  if (2u * qq + 1 < t) D[(2ull * qq + 1) * ds + slot] = (unsigned short)(r.pk[qq] >> 16);
+                }
+              } else {
+                for (unsigned int k = 0; k < t; ++k) D[k * ds + slot] = ldcg16(S + k * ss + i);
+              }
+              D[(unsigned long long)t * ds + slot] = (unsigned short)v;
+            } else {
+              set_err(p.ctl, kDevBounds, 2);
+            }
+            ++slot;
+          }
+        }
+      }
+    }
+  }
+  const unsigned long long rc = block_sum_u64(ncyc, s_red);
+  if (threadIdx.x == 0 && rc) atomicAdd(&p.hist[t + 1], rc);
+  const unsigned long long rh = block_sum_u64(hacc, s_red);
+  if (threadIdx.x == 0 && rh) atomicAdd(p.hash, rh);
+}
+
+// ------------------------------------------------------------------ the persistent kernel
+
+template <Kind K>
+__global__ void __launch_bounds__(kMaxThreads) engine_kernel(EngineParams p) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ StepPlan pl;
+  __shared__ LocalState st;
+  __shared__ unsigned int s_warp[kMaxThreads / 32 + 1];
+  __shared__ unsigned long long s_red[kMaxThreads / 32];
+  __shared__ unsigned long long s_base;
+  __shared__ __align__(8) unsigned long long s_mbar;
+  const unsigned int tid = threadIdx.x;
+
+  const unsigned long long* adj = p.adj;
+  const unsigned long long* rtab = p.rtab;
+  const unsigned int* nrow = p.nrow;
+  const unsigned short* ncol = p.ncol;
+  if (p.smem_graph) {
+    // stage the relabelled graph into shared memory with the bulk-copy (TMA) engine
+    if (tid == 0) mbar_init(&s_mbar, 1);
+    __syncthreads();
+    if (tid == 0) {
+      mbar_arrive_expect_tx(&s_mbar, p.adj_bytes + p.rtab_bytes);
+      if constexpr (KindTraits<K>::csr) {
+        bulk_copy_g2s(smem, p.nrow, p.row_bytes, &s_mbar);
+        bulk_copy_g2s(smem + p.row_bytes, p.ncol, p.adj_bytes - p.row_bytes, &s_mbar);
+      } else {
+        bulk_copy_g2s(smem, p.adj, p.adj_bytes, &s_mbar);
+      }
+      bulk_copy_g2s(smem + p.adj_bytes, p.rtab, p.rtab_bytes, &s_mbar);
+    }
+    unsigned int polls = 0;
+    while (!mbar_try_wait(&s_mbar, 0)) {
+      if (++polls > (1u << 22)) {
+        set_err(p.ctl, kDevTimeout, 2);
+        break;
+      }
+    }
+    if constexpr (KindTraits<K>::csr) {
+      nrow = reinterpret_cast<const unsigned int*>(smem);
+      ncol = reinterpret_cast<const unsigned short*>(smem + p.row_bytes);
+    } else {
+      adj = reinterpret_cast<const unsigned long long*>(smem);
+    }
+    rtab = reinterpret_cast<const unsigned long long*>(smem + p.adj_bytes);
+  }
+
+  if (tid == 0) {
+    Control* c = p.ctl;
+    if (p.fresh) {
+      const unsigned long long n0 = c->seed_count;
+      st.depth = n0 ? 1u : 0u;
+      st.bot = n0 ? p.seed_bytes : 0ull;
+      st.top = p.arena_bytes;
+      st.cur.base = 0;
+      st.cur.bytes = p.seed_bytes;
+      st.cur.stride = p.seed_stride;
+      st.cur.count = n0;
+      st.cur.cursor = 0;
+      st.cur.next = KindTraits<K>::csr ? kNoNext : c->seed_next;
+      st.cur.t = KindTraits<K>::multi ? 0u : 3u;
+      st.cur.end = 0;
+      if (blockIdx.x == 0) c->t_start = globaltimer();
+      if (blockIdx.x == 0 && n0) {
+        store_frame(&p.frames[0], st.cur);
+        if (p.seed_bytes > c->peak) c->peak = p.seed_bytes;
+      }
+    } else {
+      st.depth = c->depth;
+      st.bot = c->bot;
+      st.top = c->top;
+      if (st.depth) st.cur = load_frame(&p.frames[st.depth - 1]);
+    }
+    pl.s = c->step;
+  }
+  __syncthreads();
+  unsigned long long s = pl.s;
+  unsigned int steps_here = 0;
+  for (;;) {
+    if (tid == 0) {
+      bool go = ld_relaxed_i32(&p.ctl->err) == 0 && (p.max_steps == 0 || steps_here < p.max_steps);
+      if (go) go = plan_step<K>(p, st, pl);
+      pl.done = go ? 0u : 1u;
+      pl.s = s;
+    }
+    __syncthreads();
+    if (pl.done) break;
+    if constexpr (KindTraits<K>::csr) {
+      if (pl.t <= 16) process_csr<16>(p, pl, nrow, ncol, rtab, s_warp, s_red, &s_base);
+      else if (pl.t <= 32) process_csr<32>(p, pl, nrow, ncol, rtab, s_warp, s_red, &s_base);
+      else if (pl.t <= 64) process_csr<64>(p, pl, nrow, ncol, rtab, s_warp, s_red, &s_base);
+      else process_csr<0>(p, pl, nrow, ncol, rtab, s_warp, s_red, &s_base);
+    } else {
+      process_bitset<K>(p, pl, adj, rtab, s_warp, s_red, &s_base);
+    }
+    if (blockIdx.x == 0 && tid == 0) {
+      p.ctl->cnt[(s + 1) % 3] = 0;
+      p.ctl->nxt[(s + 1) % 3] = 0;
+    }
+    if (!grid_barrier(p.ctl, gridDim.x, p.spin_limit)) break;
+    if (tid == 0) {
+      const unsigned long long c = ld_relaxed_u64(&p.ctl->cnt[s % 3]);
+      const unsigned long long nx = ld_relaxed_u64(&p.ctl->nxt[s % 3]);
+      commit_step<K>(p, st, c, nx, blockIdx.x == 0);
+      if (blockIdx.x == 0 && p.step_ts && s < p.step_ts_cap) p.step_ts[s] = globaltimer();
+    }
+    ++s;
+    ++steps_here;
+  }
+  if (blockIdx.x == 0 && tid == 0) {
+    Control* c = p.ctl;
+    c->depth = st.depth;
+    c->bot = st.bot;
+    c->top = st.top;
+    if (st.depth) store_frame(&p.frames[st.depth - 1], st.cur);
+    c->step = s;
+  }
+}
+
+// ------------------------------------------------------------------ host-side launch helpers
+
+static const void* engine_fn(Kind k) {
+  switch (k) {
+    case Kind::Bitset1: return (const void*)engine_kernel<Kind::Bitset1>;
+    case Kind::Bitset2: return (const void*)engine_kernel<Kind::Bitset2>;
+    case Kind::Bitset4: return (const void*)engine_kernel<Kind::Bitset4>;
+    case Kind::Multi: return (const void*)engine_kernel<Kind::Multi>;
+    case Kind::Csr: return (const void*)engine_kernel<Kind::Csr>;
+  }
+  return nullptr;
+}
+
+cudaError_t engine_occupancy(Kind kind, int block, size_t smem, int* blocks_per_sm) {
+  const void* fn = engine_fn(kind);
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fn, block, smem);
+}
+
+cudaError_t launch_engine(Kind kind, const EngineParams& p, int grid, int block, size_t smem, cudaStream_t st) {
+  const void* fn = engine_fn(kind);
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  EngineParams copy = p;
+  void* args[] = {(void*)&copy};
+  return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(block), args, smem, st);
+}
+
+}  // namespace cc

@@ -1,0 +1,332 @@
+// Internal device/host definitions of the chordless-cycle library (sm_103a).
+//
+// Frontier layout.  Chordless paths in flight live in one device arena used as two
+// stacks that grow towards each other (bottom end upwards, top end downwards).  A
+// "frame" is a set of paths stored as structure-of-arrays planes inside one region;
+// expanding (part of) a frame writes the children into a new region at the OTHER end.
+// When every level fits, this is a ping-pong between the two ends, i.e. the
+// level-synchronous T -> T' step of Algorithm 3 / Algorithm 4 (Section 4.4).  When a level
+// would not fit, the frame is expanded in chunks and each chunk's subtree is finished
+// depth-first before the next chunk (bounded frontier).
+//
+// Record formats (one path per record):
+//   bitset, one graph, W = ceil(n/64) words:  B[W] (u64 planes), H (u64), M (u32)
+//       B  blocked set: union of Adj(v_i) over the interior v_2..v_{t-1}, plus every
+//          vertex whose label is <= l(v_2).  A candidate v of Adj(v_t) passes the label
+//          test and the chord test of Algorithm 3 iff v is not in B.
+//       H  sum of r(original id) over the path's vertices (running cycle-hash input).
+//       M  v_1 | v_t << 16 (relabelled ids).
+//   bitset, many graphs (n <= 64, W = 1): same planes, M = v1 | vt<<6 | t<<12 | slot<<18.
+//   CSR, one graph: t planes of u16 relabelled ids P_0..P_{t-1} (the path in order).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace cc {
+
+constexpr unsigned long long kGamma = 0x9E3779B97F4A7C15ull;
+
+// SplitMix64 output finaliser (Steele, Lea and Flood 2014; constants of Vigna's
+// public-domain splitmix64.c).  Device twin of the definition stated in cc.h.
+__host__ __device__ __forceinline__ unsigned long long mix64(unsigned long long z) {
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+__host__ __device__ __forceinline__ unsigned long long vertex_r(unsigned int v) {
+  return mix64((unsigned long long)(v + 1ull) * kGamma);
+}
+
+// Device error words (Control::err).
+enum : int {
+  kDevOk = 0,
+  kDevTimeout = 1,   // a grid barrier or an mbarrier wait hit its poll limit
+  kDevCapacity = 2,  // frontier arena too small to expand even one path
+  kDevBounds = 3,    // a write would leave its region (self-check; skipped, never done)
+  kDevDepth = 4,     // frame chain deeper than its array
+  kDevSeedCap = 5,   // initial triplets exceeded their region
+};
+
+constexpr unsigned long long kNoNext = ~0ull;
+constexpr int kMultiMaxN = 64;        // batch graphs: n <= 64, one u64 adjacency row
+constexpr int kMultiHistStride = 65;  // lengths 0..64
+constexpr unsigned kMultiMaxSlots = 1u << 14;
+constexpr unsigned kBitsetMaxN = 256;
+constexpr unsigned kCsrMaxN = 32768;
+
+struct Frame {
+  unsigned long long base;    // byte offset of the region in the arena
+  unsigned long long bytes;   // region size
+  unsigned long long stride;  // records per plane
+  unsigned long long count;   // records present
+  unsigned long long cursor;  // records already expanded
+  unsigned long long next;    // exact number of children of the whole frame, or kNoNext
+  unsigned int t;             // path length (one-graph modes); 0 = per record (batch)
+  unsigned int end;           // 0 = bottom stack, 1 = top stack
+};
+
+struct Control {
+  unsigned long long cnt[3];  // children written in step s (index s % 3)
+  unsigned long long nxt[3];  // children-of-children of step s (exact next frame size)
+  unsigned int bar_count;
+  unsigned int bar_gen;
+  int err;
+  int err_info;
+  unsigned long long step;   // global step counter (continues across launches)
+  unsigned long long bot;    // bottom stack top (bytes)
+  unsigned long long top;    // top stack bottom (bytes)
+  unsigned long long peak;   // largest extent in use (bytes)
+  unsigned int depth;        // frames in the chain
+  unsigned int spilled;      // a frame was expanded in more than one chunk
+  unsigned long long seed_count;  // initial triplets (set by the seed kernel)
+  unsigned long long seed_next;   // their children (exact)
+  unsigned long long cyc_count;   // cycles offered to the cycle list
+  unsigned long long cyc_verts;   // vertices offered to the cycle list
+  unsigned long long t_start;     // globaltimer when a fresh engine launch started
+};
+
+enum class Kind : int { Bitset1 = 0, Bitset2 = 1, Bitset4 = 2, Multi = 3, Csr = 4 };
+
+struct EngineParams {
+  unsigned char* arena;
+  unsigned long long arena_bytes;
+  Control* ctl;
+  Frame* frames;
+  unsigned int max_depth;
+  unsigned int n;        // one graph: vertices
+  unsigned int L;        // one graph: L'
+  unsigned int maxch;    // bound on children per path (max degree - 1, at least 1)
+  const unsigned long long* adj;   // bitset rows, relabelled (one graph: n*W; batch: slot*64)
+  const unsigned long long* rtab;  // r(original id) by relabelled id (one graph: n; batch: slot*64)
+  const unsigned int* nrow;        // CSR (one graph): relabelled row offsets [n+1]
+  const unsigned short* ncol;      // CSR: relabelled sorted neighbours
+  unsigned char* Lg;               // batch: L' per slot
+  const unsigned int* perm;        // one graph: relabelled id -> original id
+  unsigned long long* hist;        // one graph: [L+1]; batch: [slot*65 + k]
+  unsigned long long* hash;        // one graph: [1]; batch: [slot]
+  unsigned long long* tcount;      // one graph: [L+1]; batch: [slot*65 + t]
+  unsigned int* last_step;         // batch: last step that expanded a path of the slot
+  long long* live;                 // batch/serving: paths of the slot still in flight
+  unsigned long long* step_ts;     // globaltimer at the end of each step (optional)
+  unsigned int step_ts_cap;
+  unsigned int max_steps;          // stop after this many steps in this launch (0 = no limit)
+  unsigned long long reserve;      // extra child capacity reserved for admissions (records)
+  unsigned int spin_limit;
+  unsigned int smem_graph;         // 1: graph data staged in shared memory
+  unsigned int adj_bytes;          // bytes staged for adjacency (bitset) / rows+cols (CSR)
+  unsigned int rtab_bytes;
+  unsigned int seed_entries;       // CSR seeding: number of directed entries (2m)
+  unsigned int* cyc_vert;          // cycle list (CSR path only): vertices, original ids
+  unsigned long long* cyc_start;   // cycle i starts at cyc_vert[cyc_start[i]]
+  unsigned int* cyc_len;           // and has cyc_len[i] vertices
+  unsigned long long cyc_cap_c, cyc_cap_v;
+  unsigned int fresh;              // 1: build frame 0 from the seed counters at kernel start
+  unsigned int row_bytes;          // CSR staging: bytes of the row offsets (16-byte padded)
+  unsigned long long seed_stride;  // frame 0 records per plane
+  unsigned long long seed_bytes;   // frame 0 region bytes
+};
+
+#ifdef __CUDACC__
+// Cycle list entry in canonical order (original ids): smallest id first, then towards
+// its smaller cycle neighbour.  vtx(j) returns the relabelled id of cycle position j.
+template <typename F>
+__device__ __forceinline__ void emit_cycle(const EngineParams& p, unsigned int k, F vtx) {
+  unsigned int i0 = 0, best = p.perm[vtx(0)];
+  for (unsigned int i = 1; i < k; ++i) {
+    const unsigned int o = p.perm[vtx(i)];
+    if (o < best) best = o, i0 = i;
+  }
+  const unsigned int nx = p.perm[vtx((i0 + 1) % k)], pv = p.perm[vtx((i0 + k - 1) % k)];
+  const bool fwd = nx < pv;
+  const unsigned long long ci = atomicAdd(&p.ctl->cyc_count, 1ull);
+  const unsigned long long vb = atomicAdd(&p.ctl->cyc_verts, (unsigned long long)k);
+  if (ci < p.cyc_cap_c && vb + k <= p.cyc_cap_v) {
+    for (unsigned int j = 0; j < k; ++j) {
+      const unsigned int idx = fwd ? (i0 + j) % k : (i0 + k - j) % k;
+      p.cyc_vert[vb + j] = p.perm[vtx(idx)];
+    }
+    p.cyc_start[ci] = vb;
+    p.cyc_len[ci] = k;
+  }
+}
+#endif
+
+// ------------------------------------------------------------------ small device helpers
+#ifdef __CUDACC__
+
+__device__ __forceinline__ unsigned long long ldcg64(const unsigned long long* p) { return __ldcg(p); }
+__device__ __forceinline__ unsigned int ldcg32(const unsigned int* p) { return __ldcg(p); }
+__device__ __forceinline__ unsigned short ldcg16(const unsigned short* p) { return __ldcg(p); }
+
+__device__ __forceinline__ unsigned int ld_acquire_u32(const unsigned int* p) {
+  unsigned int v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ int ld_relaxed_i32(const int* p) {
+  int v;
+  asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_u32(unsigned int* p, unsigned int v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long globaltimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void set_err(Control* ctl, int code, int info) {
+  if (atomicCAS(&ctl->err, 0, code) == 0) ctl->err_info = info;
+}
+
+// Grid-wide barrier for a cooperative (co-resident) launch, with a bounded wait.
+// Returns false if this block gave up waiting or any block has reported an error;
+// every block then leaves its step loop, so the kernel always terminates.
+__device__ __forceinline__ bool grid_barrier(Control* ctl, unsigned int nblocks, unsigned int spin_limit) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    unsigned int gen = ld_acquire_u32(&ctl->bar_gen);
+    __threadfence();
+    unsigned int arrived = atomicAdd(&ctl->bar_count, 1u);
+    if (arrived == nblocks - 1) {
+      atomicExch(&ctl->bar_count, 0u);
+      __threadfence();
+      st_release_u32(&ctl->bar_gen, gen + 1);
+    } else {
+      unsigned int polls = 0;
+      while (ld_acquire_u32(&ctl->bar_gen) == gen) {
+        if (ld_relaxed_i32(&ctl->err) != 0) { ok = 0; break; }
+        if (++polls > spin_limit) { set_err(ctl, kDevTimeout, 1); ok = 0; break; }
+        if (polls > 32) __nanosleep(polls > 4096 ? 256 : 32);
+      }
+    }
+    if (ld_relaxed_i32(&ctl->err) != 0) ok = 0;
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+// Exclusive block-wide prefix sum of v; *total receives the block sum.
+// s_warp must hold blockDim.x/32 + 1 words; callers separate consecutive calls by a
+// __syncthreads (this function ends with one).
+__device__ __forceinline__ unsigned int block_exclusive_scan(unsigned int v, unsigned int* total,
+                                                             unsigned int* s_warp) {
+  const unsigned lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  unsigned int x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    unsigned int y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= (unsigned)o) x += y;
+  }
+  if (lane == 31) s_warp[wid] = x;
+  __syncthreads();
+  if (wid == 0) {
+    unsigned int w = lane < nw ? s_warp[lane] : 0u;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      unsigned int y = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= (unsigned)o) w += y;
+    }
+    if (lane < nw) s_warp[lane] = w;
+  }
+  __syncthreads();
+  unsigned int before = wid ? s_warp[wid - 1] : 0u;
+  *total = s_warp[nw - 1];
+  __syncthreads();
+  return before + x - v;
+}
+
+__device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block-wide sum of a u64 (result valid in thread 0).  s_red holds blockDim.x/32 words.
+__device__ __forceinline__ unsigned long long block_sum_u64(unsigned long long v, unsigned long long* s_red) {
+  const unsigned lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  v = warp_sum_u64(v);
+  __syncthreads();
+  if (lane == 0) s_red[wid] = v;
+  __syncthreads();
+  unsigned long long r = 0;
+  if (wid == 0) {
+    r = lane < nw ? s_red[lane] : 0ull;
+    r = warp_sum_u64(r);
+  }
+  return r;
+}
+
+// ---- bulk (TMA engine, non-tensor) global->shared staging with an mbarrier
+__device__ __forceinline__ unsigned int smem_addr(const void* p) {
+  return (unsigned int)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned int count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(unsigned long long* bar, unsigned int bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, unsigned int bytes,
+                                              unsigned long long* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(bar))
+      : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned int parity) {
+  unsigned int ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+#endif  // __CUDACC__
+
+// ------------------------------------------------------------------ host-side sizes
+__host__ __device__ __forceinline__ unsigned long long round_up(unsigned long long x, unsigned long long a) {
+  return (x + a - 1) / a * a;
+}
+// Record bytes: bitset planes (8W + 12), CSR planes (2t).
+__host__ __device__ __forceinline__ unsigned long long bitset_region_bytes(unsigned long long stride, int W) {
+  return round_up(stride * (8ull * W + 12ull), 256);
+}
+__host__ __device__ __forceinline__ unsigned long long csr_region_bytes(unsigned long long stride, unsigned t) {
+  return round_up(stride * 2ull * t, 256);
+}
+
+// Kernel launchers (defined in the .cu files).
+cudaError_t launch_label_single(const unsigned int* row_ptr, const unsigned int* col, unsigned int n,
+                                int W, unsigned int* perm, unsigned long long* adj,
+                                unsigned long long* rtab, unsigned int* nrow, unsigned short* ncol,
+                                cudaStream_t st);
+cudaError_t launch_seed_single(Kind kind, const EngineParams& p, unsigned long long seed_stride,
+                               cudaStream_t st);
+cudaError_t launch_engine(Kind kind, const EngineParams& p, int grid, int block, size_t smem,
+                          cudaStream_t st);
+cudaError_t engine_occupancy(Kind kind, int block, size_t smem, int* blocks_per_sm);
+size_t engine_smem_bytes(Kind kind, const EngineParams& p, int block);
+cudaError_t launch_label_seed_multi(const unsigned int* row_ptr_all, const unsigned long long* row_off,
+                                    const unsigned int* col_all, const unsigned long long* col_off,
+                                    const unsigned int* n_arr, unsigned int count, unsigned int slot0,
+                                    unsigned int max_len, const EngineParams& p, unsigned long long frame_base,
+                                    unsigned long long stride, unsigned long long* slot_counter,
+                                    unsigned long long* next_counter, cudaStream_t st);
+
+}  // namespace cc

@@ -1,0 +1,281 @@
+"""CUDA path against the CPU oracle, element by element, through the C ABI.
+
+Integer results, so the bar is bit-exact: per-length histogram, total, 64-bit cycle hash,
+per-length stored-path counts (same degree labelling and tie rule on both sides) and,
+where requested, the canonical cycle lists.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1410_4876_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def cc():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1410_4876_gb300 import cc as _cc
+    _cc.load_library()
+    return _cc
+
+
+@pytest.fixture(scope="module")
+def ctx(cc):
+    c = cc.Context(frontier_bytes=4 << 30)
+    yield c
+    c.close()
+
+
+def _same(r, ref, tcount=True):
+    assert r.hist.tolist() == ref.hist.tolist()
+    assert r.hash == ref.hash
+    if tcount:
+        assert r.tcount.tolist() == ref.tcount.tolist()
+
+
+def _small_graphs(count, seed0):
+    out = []
+    for s in range(count):
+        n = 3 + s % 20
+        p = [0.1, 0.2, 0.35, 0.5, 0.8][s % 5]
+        out.append(I.gnp(n, p, seed0 + s))
+    return out
+
+
+def test_small_random_graphs(ctx):
+    for g in _small_graphs(200, 4242):
+        _same(ctx.enumerate(g), oracle.enumerate_cycles(g))
+
+
+@pytest.mark.parametrize("g", [I.gnp(65, 2.6 / 65, 65), I.gnp(100, 2.4 / 100, 100), I.gnp(128, 2.4 / 128, 128),
+                               I.gnp(129, 2.6 / 129, 129), I.gnp(200, 1.9 / 200, 200), I.gnp(256, 1.8 / 256, 256),
+                               I.complete_bipartite(40, 40), I.wheel(200), I.cycle(250)], ids=lambda g: g.name)
+def test_bitset_widths(ctx, g):
+    # two- and four-word bitset rows, and the boundaries between the widths (sparse random
+    # graphs much denser than these have far too many chordless paths to enumerate)
+    _same(ctx.enumerate(g), oracle.enumerate_cycles(g))
+
+
+@pytest.mark.parametrize("g", [I.grid(6, 6), I.grid(4, 10), I.grid(5, 6), I.grid(5, 10), I.complete_bipartite(8, 8),
+                               I.cycle(100), I.wheel(100), I.complete_bipartite(50, 50), I.complete(20)],
+                         ids=lambda g: g.name)
+def test_table1_graphs(ctx, g):
+    _same(ctx.enumerate(g), oracle.enumerate_cycles(g))
+
+
+def test_grid6x10_table1(ctx):
+    r = ctx.enumerate(I.grid(6, 10))
+    assert r.total == 800139  # Table 1
+
+
+@pytest.mark.parametrize("max_len", [1, 2, 3, 4, 5, 8, 13])
+def test_length_bound(ctx, max_len):
+    for g in [I.grid(5, 5), I.gnp(40, 0.12, 3), I.wheel(12), I.gnp(150, 0.022, 9)]:
+        _same(ctx.enumerate(g, max_len=max_len), oracle.enumerate_cycles(g, max_len=max_len))
+
+
+def test_edge_cases(ctx):
+    for g in [I.empty(0), I.empty(1), I.empty(2), I.empty(10), I.path(2), I.path(30), I.complete(3),
+              I.cycle(3), I.cycle(4), I.random_tree(40, 1), I.random_unicyclic(50, 2),
+              I.from_edges(9, [(0, 1), (1, 2), (2, 0), (4, 5), (5, 6), (6, 7), (7, 4)])]:
+        r = ctx.enumerate(g)
+        ref = oracle.enumerate_cycles(g)
+        _same(r, ref)
+
+
+def test_invalid_graphs(cc, ctx):
+    bad = [
+        (3, [0, 1, 1, 1], [1]),               # 0 -> 1 without 1 -> 0
+        (2, [0, 1, 2], [0, 1]),               # self-loops
+        (3, [0, 2, 3, 4], [1, 1, 0, 0]),      # duplicate neighbour
+        (2, [0, 1, 2], [5, 0]),               # id out of range
+        (2, [0, 2, 1], [1, 0]),               # decreasing row_ptr
+    ]
+    for n, rp, cl in bad:
+        s, h = cc.cc_graph_load(ctx.handle, n, np.array(rp, np.uint32), np.array(cl, np.uint32))
+        assert s == cc.CC_ERR_INVALID_GRAPH, (n, rp, cl, s)
+
+
+def test_unsorted_rows_accepted(ctx):
+    g = I.grid(4, 4)
+    rp, cl = g.row_ptr.copy(), g.col.copy()
+    for v in range(g.n):
+        cl[rp[v]:rp[v + 1]] = cl[rp[v]:rp[v + 1]][::-1]
+    g2 = I.Graph(g.n, rp, cl)
+    _same(ctx.enumerate(g2), oracle.enumerate_cycles(g))
+
+
+def test_csr_mode_equals_bitset_mode(cc):
+    with cc.Context(frontier_bytes=1 << 30, mode=cc.CC_MODE_CSR) as c:
+        for g in _small_graphs(60, 99) + [I.grid(6, 6), I.wheel(30), I.complete_bipartite(6, 7)]:
+            r = c.enumerate(g)
+            assert r.info.mode == cc.CC_MODE_CSR
+            _same(r, oracle.enumerate_cycles(g))
+
+
+def test_cycle_lists(ctx):
+    for g in _small_graphs(40, 7) + [I.grid(4, 5), I.wheel(9), I.complete(6), I.cycle(40)]:
+        r = ctx.enumerate(g, cycles=True)
+        ref = oracle.enumerate_cycles(g, cycles=True)
+        assert sorted(r.cycles) == sorted(ref.cycles)
+        _same(r, ref)
+
+
+def test_cycle_list_truncation(cc, ctx):
+    g = I.grid(4, 4)
+    with ctx.load(g) as lg:
+        s, hist, h, tc, cyc, info = cc.cc_enumerate(lg.handle, g.n, 0, True, (3, 10))
+        assert s == cc.CC_ERR_TRUNCATED
+        ref = oracle.enumerate_cycles(g)
+        assert cyc == (ref.total, int(sum(k * int(c) for k, c in enumerate(ref.hist))))
+        assert hist.tolist() == ref.hist.tolist() and h == ref.hash
+
+
+@pytest.mark.parametrize("budget", [256 << 10, 1 << 20, 64 << 20])
+def test_bounded_frontier_spill(cc, budget):
+    # grid 7x7 peaks at 80,935 stored paths (20 bytes each, two levels live at once);
+    # budgets far below that force depth-first chunks, 64 MiB does not
+    g = I.grid(7, 7)
+    ref = oracle.enumerate_cycles(g)
+    with cc.Context(frontier_bytes=budget) as c:
+        r = c.enumerate(g)
+    _same(r, ref)
+    assert r.info.spilled == (1 if budget <= 1 << 20 else 0)
+    assert r.info.peak_bytes <= budget
+
+
+def test_spill_csr(cc):
+    g = I.gnm(400, 800, 5)
+    ref = oracle.enumerate_cycles(g, max_len=10)
+    with cc.Context(frontier_bytes=2 << 20) as c:
+        r = c.enumerate(g, max_len=10)
+    _same(r, ref)
+    assert r.info.spilled == 1
+
+
+def test_capacity_error(cc):
+    # the initial triplets of K_{50,50} (up to (Delta-1)m/2 = 61250 paths) cannot fit 64 KiB
+    with cc.Context(frontier_bytes=1 << 16) as c:
+        with pytest.raises(cc.CCError) as e:
+            c.enumerate(I.complete_bipartite(50, 50))
+        assert e.value.status == cc.CC_ERR_CAPACITY
+        # the context stays usable
+        _same(c.enumerate(I.grid(3, 3)), oracle.enumerate_cycles(I.grid(3, 3)))
+
+
+def test_barrier_timeout_reports_status(cc):
+    # a poll limit of one makes the grid barrier give up at once: the call must return
+    # CC_ERR_TIMEOUT (no fault, no hang) and a later call on a fresh context must work
+    with cc.Context(spin_limit=1) as c:
+        with pytest.raises(cc.CCError) as e:
+            c.enumerate(I.grid(6, 6))
+        assert e.value.status == cc.CC_ERR_TIMEOUT
+    with cc.Context() as c:
+        _same(c.enumerate(I.grid(6, 6)), oracle.enumerate_cycles(I.grid(6, 6)))
+
+
+def test_torch_workspace_and_stream(cc):
+    import torch
+    with cc.Context(frontier_bytes=256 << 20, use_torch=True) as c:
+        g = I.gnp(50, 0.12, 1)
+        _same(c.enumerate(g), oracle.enumerate_cycles(g))
+    torch.cuda.synchronize()
+
+
+def test_relabelling_invariance(ctx):
+    g = I.gnp(45, 0.15, 17)
+    perm = I.random_permutation(g.n, 5)
+    a = ctx.enumerate(g, cycles=True)
+    b = ctx.enumerate(I.permute(g, perm), cycles=True)
+    assert a.hist.tolist() == b.hist.tolist()
+    assert sorted(tuple(sorted(int(perm[v]) for v in c)) for c in a.cycles) == \
+        sorted(tuple(sorted(c)) for c in b.cycles)
+
+
+# ------------------------------------------------------------------ full-size workloads
+
+def test_grid8x8_full(ctx):
+    g = I.grid(8, 8)
+    _same(ctx.enumerate(g), oracle.enumerate_parallel(g))
+
+
+def test_gnp60_full(ctx):
+    g = I.gnp(60, 0.15, 7)
+    _same(ctx.enumerate(g), oracle.enumerate_parallel(g))
+
+
+def test_gnm2000_len12_full(ctx):
+    g = I.gnm(2000, 4000, 11)
+    r = ctx.enumerate(g, max_len=12)
+    assert r.info.mode == 2  # CSR path: n = 2000 does not fit the bitset rows
+    _same(r, oracle.enumerate_parallel(g, max_len=12))
+
+
+# ------------------------------------------------------------------ batches
+
+def _oracle_many(graphs, max_len=0):
+    import concurrent.futures as cf
+    import os
+    with cf.ThreadPoolExecutor(os.cpu_count() or 4) as ex:
+        return list(ex.map(lambda g: oracle.enumerate_cycles(g, max_len=max_len), graphs))
+
+
+def _check_batch(graphs, refs, hist, hsh, paths):
+    for i, (g, ref) in enumerate(zip(graphs, refs)):
+        L = len(ref.hist) - 1
+        assert hist[i, :L + 1].tolist() == ref.hist.tolist(), (i, g.name)
+        assert int(hist[i, L + 1:].sum()) == 0
+        assert int(hsh[i]) == ref.hash, (i, g.name)
+        assert int(paths[i]) == int(ref.tcount.sum()), (i, g.name)
+
+
+def test_batch_mixture(ctx):
+    graphs = I.mixture(400, 31)
+    hist, hsh, paths, done, info = ctx.batch(graphs, max_len=7)
+    _check_batch(graphs, _oracle_many(graphs, 7), hist, hsh, paths)
+
+
+def test_batch_mixture_unbounded_small(ctx):
+    graphs = [g for g in I.mixture(300, 8) if g.n <= 30]
+    hist, hsh, paths, done, info = ctx.batch(graphs)
+    _check_batch(graphs, _oracle_many(graphs), hist, hsh, paths)
+
+
+def test_batch_full_mixture_sampled(ctx):
+    # the full 4096-graph mixture in one launch; every K_{a,b} against its closed form,
+    # every grid and a seeded sample of the random graphs against the oracle
+    graphs = I.mixture(4096, 0)
+    hist, hsh, paths, done, info = ctx.batch(graphs)
+    for i, g in enumerate(graphs):
+        if g.meta["family"] == "kab":
+            a, b = g.meta["a"], g.meta["b"]
+            assert int(hist[i, 4]) == int(hist[i].sum()) == (a * (a - 1) // 2) * (b * (b - 1) // 2)
+    pick = [i for i, g in enumerate(graphs) if g.meta["family"] == "grid"]
+    rng = np.random.default_rng(2024)
+    gnp_idx = [i for i, g in enumerate(graphs) if g.meta["family"] == "gnp"]
+    pick += sorted(rng.choice(gnp_idx, 24, replace=False).tolist())
+    sub = [graphs[i] for i in pick]
+    _check_batch(sub, _oracle_many(sub), hist[pick], hsh[pick], paths[pick])
+    assert (done >= 0).all()
+
+
+def test_batch_alone_equals_mixed(ctx):
+    graphs = I.mixture(64, 77)
+    hist, hsh, paths, done, info = ctx.batch(graphs, max_len=9)
+    for i in range(0, 64, 7):
+        h1, s1, p1, _, _ = ctx.batch([graphs[i]], max_len=9)
+        assert h1[0].tolist() == hist[i].tolist() and s1[0] == hsh[i] and p1[0] == paths[i]
+        r = ctx.enumerate(graphs[i], max_len=9)
+        assert r.hist.tolist() == hist[i, :len(r.hist)].tolist() and r.hash == int(hsh[i])
+
+
+def test_batch_spill(cc):
+    graphs = I.mixture(48, 5)
+    with cc.Context(frontier_bytes=3 << 20) as c:
+        hist, hsh, paths, done, info = c.batch(graphs, max_len=8)
+    assert info.spilled == 1
+    _check_batch(graphs, _oracle_many(graphs, 8), hist, hsh, paths)
