@@ -203,6 +203,38 @@ cc_status cc_batch_poll(cc_context* ctx, cc_batch_id batch, uint32_t timeout_us,
                         uint32_t hist_stride, uint64_t* hash, uint64_t* paths, double* done_us,
                         cc_run_info* info);
 
+/*
+ * Allocation-free enumeration (the paper has no counterpart; this is a deployment aid).
+ *
+ * For callers that cannot allocate memory while they run: a plugin or real-time loop whose
+ * host application forbids device allocations after start-up, a process whose device
+ * memory is owned by another pool allocator, or a latency-critical path where
+ * cudaMalloc's implicit device-wide synchronisation would stall other streams.  It does
+ * what cc_enumerate does for one graph with n <= CC_NOALLOC_MAX_N, but allocates nothing
+ * (no cudaMalloc/cudaFree of any kind, no host heap): all device memory it uses is one
+ * fixed device array of CC_NOALLOC_SCRATCH_BYTES inside this library, which every GPU that
+ * loads the library holds until the process exits.  The frontier gets what the array's
+ * fixed layout leaves (about 63 MiB); larger levels are expanded in depth-first chunks.
+ *
+ *   n, row_ptr, col_idx  host CSR as for cc_graph_load, except that every row must already
+ *                        be sorted ascending (nothing is copied to sort it); otherwise
+ *                        CC_ERR_INVALID_GRAPH
+ *   max_len              as for cc_enumerate
+ *   stream               cudaStream_t to run on (NULL = default stream); the call returns
+ *                        after the stream has finished its work
+ *   out_hist, out_hash, out_tcount   host outputs as for cc_enumerate (out_tcount may be NULL)
+ * Errors: CC_ERR_UNSUPPORTED if n > CC_NOALLOC_MAX_N, CC_ERR_CAPACITY if the initial triplets
+ * cannot fit the array, CC_ERR_ARG, CC_ERR_CUDA, CC_ERR_TIMEOUT.
+ * The array's device address is looked up (cudaGetSymbolAddress) on the first call on each
+ * device, so make that first call before any stream capture.  All calls share the array and
+ * each call clears the parts that must start at zero; calls whose GPU work overlaps (other
+ * streams or host threads) race on it and must be serialised by the caller.
+ */
+#define CC_NOALLOC_MAX_N 256
+#define CC_NOALLOC_SCRATCH_BYTES (64ull << 20)
+cc_status cc_enumerate_noalloc(uint32_t n, const uint32_t* row_ptr, const uint32_t* col_idx, uint32_t max_len,
+                               void* stream, uint64_t* out_hist, uint64_t* out_hash, uint64_t* out_tcount);
+
 #ifdef __cplusplus
 }
 #endif

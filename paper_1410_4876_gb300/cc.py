@@ -112,6 +112,8 @@ SIGNATURES = {
                                          ctypes.c_uint32, _u64p]),
     "cc_batch_poll": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32, _u64p, ctypes.c_uint32,
                                        _u64p, _u64p, _dblp, ctypes.POINTER(cc_run_info)]),
+    "cc_enumerate_noalloc": (ctypes.c_int32, [ctypes.c_uint32, _u32p, _u32p, ctypes.c_uint32, ctypes.c_void_p,
+                                              _u64p, _u64p, _u64p]),
 }
 
 
