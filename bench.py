@@ -3,7 +3,7 @@
 Default workload (one step): full enumeration of the 8 x 8 grid graph and of the seeded
 Erdos-Renyi graph G(n=60, p=0.15, seed 7), all cycle lengths, through the C ABI
 (cc_enumerate on graphs already resident in HBM).  Between timed steps the L2 cache is
-flushed by writing a 512 MiB buffer.
+flushed by writing a 256 MiB buffer (about twice the L2).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                   [--workload grid8+gnp60|grid6|gnm2000|batch]
@@ -194,8 +194,8 @@ def run_ours(args, work, desc):
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
     # run on torch's stream so events, the L2 flush and the library share one stream
-    ctx = cc.Context(frontier_bytes=8 << 30, stream=stream.cuda_stream)
-    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    ctx = cc.Context(frontier_bytes=args.frontier_mb << 20, stream=stream.cuda_stream)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # twice the 129 MB L2
     loaded = [(ctx.load(g), L, g) for g, L in work]
 
     def step():
@@ -267,7 +267,7 @@ def run_ours(args, work, desc):
         "metric": "chordless cycles/s", "value": value, "unit": "cycles/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-        "config": {"workload": desc, "l2": "flushed between steps (512 MiB write)",
+        "config": {"workload": desc, "l2": "flushed between steps (256 MiB write)",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                    "cycles_per_step": cycles // args.steps, "paths_per_step": paths // args.steps},
         "paths_expanded_per_s": world * paths / (t_ms / 1000.0),
@@ -293,6 +293,127 @@ def run_ours(args, work, desc):
         dist.destroy_process_group()
 
 
+def _percentiles(x):
+    x = np.asarray(x, dtype=np.float64)
+    if x.size == 0:
+        return None, None
+    return float(np.percentile(x, 50)), float(np.percentile(x, 99))
+
+
+def run_batch(args):
+    """4096 graphs of the batch mixture (seed 0) in one persistent launch, against plain
+    per-graph cc_enumerate calls of the same graphs."""
+    import torch
+
+    from paper_1410_4876_gb300 import cc
+    graphs = I.mixture(args.batch_count, 0)
+    ctx = cc.Context(frontier_bytes=args.frontier_mb << 20)
+    for _ in range(args.warmup):
+        ctx.batch(graphs[:256])
+    torch.cuda.synchronize()
+    times, cyc, paths, p50, p99 = [], 0, 0, None, None
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        hist, hsh, pth, done, info = ctx.batch(graphs)
+        times.append(time.perf_counter() - t0)
+        cyc, paths = int(hist.sum()), int(pth.sum())
+        p50, p99 = _percentiles(done / 1000.0)
+        eng_ms = info.ms_engine
+    t = min(times)
+    # plain per-graph launches (label + seed + expansion kernels per graph), same graphs
+    loaded = [ctx.load(g) for g in graphs]
+    t0 = time.perf_counter()
+    seq_cyc = 0
+    for lg in loaded:
+        seq_cyc += lg.enumerate().total
+    t_seq = time.perf_counter() - t0
+    for lg in loaded:
+        lg.close()
+    assert seq_cyc == cyc
+    line = {
+        "metric": "chordless cycles/s (batched)", "value": cyc / t, "unit": "cycles/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * t, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": f"{len(graphs)} graphs of the seeded batch mixture (50% G(n,p), 30% grids, "
+                               "20% K_ab), all lengths", "cycles": cyc, "paths": paths},
+        "paths_expanded_per_s": paths / t, "engine_ms": eng_ms,
+        "per_graph_done_ms": {"p50": p50, "p99": p99},
+        "per_graph_launches": {"value": seq_cyc / t_seq, "unit": "cycles/s", "seconds": t_seq},
+        "batched_over_per_graph": (cyc / t) / (seq_cyc / t_seq),
+    }
+    ctx.close()
+    print(json.dumps(line), flush=True)
+
+
+def run_serve(args):
+    """Poisson arrivals (seed 3) of serving requests, continuous batching, p50/p99."""
+    import torch
+
+    from paper_1410_4876_gb300 import cc
+    arrivals = I.poisson_arrivals(args.rate, args.serve_seconds, 3)
+    reqs = [I.make(*I.serving_request(i, 3)) for i in range(len(arrivals))]
+    n_req = len(reqs)
+    ctx = cc.Context(frontier_bytes=args.frontier_mb << 20)
+    srv = cc.Server(ctx, slots=4096, steps_per_round=args.serve_steps, admit_bytes=64 << 30)
+    # warm up the kernels on a few requests
+    for g in reqs[:8]:
+        srv.submit(g)
+    left = 8
+    while left:
+        d, _, _ = srv.step()
+        left -= len(d)
+    torch.cuda.synchronize()
+    ids, lat, waits = {}, [], []
+    cyc = paths = 0
+    i = 0
+    finished = 0
+    rounds = 0
+    t0 = time.perf_counter()
+    while finished < n_req:
+        now = time.perf_counter() - t0
+        while i < n_req and arrivals[i] <= now:
+            ids[srv.submit(reqs[i])] = i
+            i += 1
+        done, inflight, queued = srv.step()
+        rounds += 1
+        tnow = time.perf_counter() - t0
+        for d in done:
+            k = ids.pop(d["id"])
+            lat.append(tnow - arrivals[k])
+            waits.append(d["wait_us"] / 1e6)
+            cyc += d["total"]
+            paths += d["paths"]
+        finished += len(done)
+        if inflight == 0 and queued == 0 and i < n_req:
+            while time.perf_counter() - t0 < arrivals[i]:
+                pass
+    elapsed = time.perf_counter() - t0
+    srv.close()
+    p50, p99 = _percentiles(np.array(lat) * 1000)
+    w50, w99 = _percentiles(np.array(waits) * 1000)
+    # plain sequential per-graph launches on a prefix of the same stream
+    k = min(n_req, args.seq_sample)
+    t1 = time.perf_counter()
+    seq_c = 0
+    for g in reqs[:k]:
+        seq_c += ctx.enumerate(g).total
+    t_seq = time.perf_counter() - t1
+    ctx.close()
+    line = {
+        "metric": "served chordless cycles/s", "value": cyc / elapsed, "unit": "cycles/s", "n_gpus": 1,
+        "steps": rounds, "warmup": 1, "ms_per_step": 1000 * elapsed / max(rounds, 1), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": f"Poisson arrivals, mean {args.rate}/s for {args.serve_seconds} s (seed 3): "
+                               "95% batch-mixture graphs + 5% 8x8 grids; admission budget 64 GiB",
+                   "requests": n_req, "steps_per_round": args.serve_steps},
+        "offered_requests_per_s": n_req / args.serve_seconds, "achieved_requests_per_s": n_req / elapsed,
+        "elapsed_s": elapsed, "paths_expanded_per_s": paths / elapsed,
+        "latency_ms": {"p50": p50, "p99": p99}, "queue_wait_ms": {"p50": w50, "p99": w99},
+        "sequential_per_graph": {"requests": k, "requests_per_s": k / t_seq, "cycles_per_s": seq_c / t_seq},
+    }
+    print(json.dumps(line), flush=True)
+
+
 def _ncu_traffic():
     """DRAM bytes per launch of the expansion kernel from the committed ncu summary, when
     the summary was taken on the current kernel (the summary records it); else None."""
@@ -312,9 +433,19 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="grid8+gnp60", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="grid8+gnp60", choices=sorted(WORKLOADS) + ["batch", "serve"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the cpu_baseline leg")
+    ap.add_argument("--frontier-mb", type=int, default=8192, help="device memory for paths in flight (MiB)")
+    ap.add_argument("--batch-count", type=int, default=4096)
+    ap.add_argument("--rate", type=float, default=2000.0, help="serving: mean arrivals per second")
+    ap.add_argument("--serve-seconds", type=float, default=10.0, help="serving: arrival window (s)")
+    ap.add_argument("--serve-steps", type=int, default=8, help="serving: expansion steps per round")
+    ap.add_argument("--seq-sample", type=int, default=2000, help="serving: requests timed one by one")
     args = ap.parse_args()
+    if args.workload == "batch":
+        return run_batch(args)
+    if args.workload == "serve":
+        return run_serve(args)
     desc, make = WORKLOADS[args.workload]
     work = make()
     if args.impl == "reference":

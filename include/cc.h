@@ -171,6 +171,17 @@ cc_status cc_enumerate(cc_graph* g, uint32_t max_len, uint64_t* out_hist, uint64
                        uint64_t* out_tcount, cc_cycles* out_cycles, cc_run_info* out_info);
 
 /*
+ * Per-step trace of the last cc_enumerate on this context (Section 5, Fig. 4 of the paper
+ * plots the size of T per step).  Step i expands a set of stored paths of one length (a
+ * whole level, or a chunk of one when the frontier budget forces depth-first chunks).
+ *   cap       entries available in t_ns and expanded (0: only *n_steps is filled)
+ *   t_ns      device time (ns) from the start of the expansion to the end of step i
+ *   expanded  paths expanded in step i
+ *   n_steps   steps of the last call (at most 65536 are recorded)
+ */
+cc_status cc_get_trace(cc_context* ctx, uint32_t cap, uint64_t* t_ns, uint64_t* expanded, uint64_t* n_steps);
+
+/*
  * Batched enumeration: `count` graphs packed back to back, all enumerated by one
  * persistent launch whose frontier mixes paths of every graph.
  *   n[g]        vertices of graph g (each <= cc_limits.max_n_batch)
@@ -202,6 +213,63 @@ cc_status cc_batch_submit(cc_context* ctx, uint32_t count, const uint32_t* n,
 cc_status cc_batch_poll(cc_context* ctx, cc_batch_id batch, uint32_t timeout_us, uint64_t* hist,
                         uint32_t hist_stride, uint64_t* hash, uint64_t* paths, double* done_us,
                         cc_run_info* info);
+
+/*
+ * Serving: a request loop with continuous batching (the paper has no counterpart; it
+ * serves many graphs with the same level-synchronous expansion).
+ *
+ * Requests (graphs with n <= 64) are queued by cc_serve_submit.  Each cc_serve_step
+ *   1. collects every in-flight request whose last path has been expanded (its result is
+ *      copied to the host and its slot freed),
+ *   2. admits queued requests in arrival order while a slot is free, the sum of the
+ *      admitted requests' predicted frontier bytes stays within admit_bytes, and their
+ *      initial triplets fit the space reserved in the live frontier; their triplets join
+ *      the frontier that the running requests' paths are in,
+ *   3. runs up to steps_per_round expansion steps over that shared frontier (paths of
+ *      every admitted request, whatever their length), then returns.
+ * Results are bit-identical to cc_enumerate on the same graph; only the timing depends on
+ * the mix.  A request's predicted bytes come from the caller or, when 0, from a
+ * predictor built into the library (a fit of peak stored paths against n, m and the
+ * maximum degree on seeded random, grid and complete bipartite graphs).  A
+ * misprediction costs only memory: a frontier that would not fit is expanded in
+ * depth-first chunks.  One server per context; not thread safe.
+ */
+typedef struct cc_server cc_server;
+typedef struct cc_serve_options {
+  uint32_t slots;            /* requests in flight at most (<= 16384; 0 = 4096)            */
+  uint32_t max_len;          /* cycle length bound for every request (0 = none)            */
+  uint64_t admit_bytes;      /* admission budget of predicted frontier bytes (0 = 64 GiB)  */
+  uint32_t steps_per_round;  /* expansion steps per cc_serve_step (0 = 8)                  */
+  uint32_t pad;
+  uint64_t reserve_paths;    /* frontier capacity kept free per step for admissions (0 = 2^18) */
+} cc_serve_options;
+
+typedef struct cc_completion {
+  uint64_t id;           /* as returned by cc_serve_submit                           */
+  uint64_t hash;         /* cycle hash (as cc_enumerate)                             */
+  uint64_t total;        /* chordless cycles                                         */
+  uint64_t paths;        /* stored chordless paths                                   */
+  uint64_t hist[65];     /* hist[k], k <= min(L', 64)                                */
+  double wait_us;        /* submit -> admission                                      */
+  double latency_us;     /* submit -> result on the host                             */
+} cc_completion;
+
+/* Create a server on a context (its frontier arena is shared with cc_enumerate calls on
+ * the same context, which must not run while the server has requests in flight). */
+cc_status cc_serve_create(cc_context* ctx, const cc_serve_options* opts, cc_server** out);
+void cc_serve_destroy(cc_server* srv);
+/* Queue a request (host CSR as for cc_graph_load, n <= 64; copied).  predicted_bytes = 0
+ * uses the built-in predictor.  *out_id receives the request id. */
+cc_status cc_serve_submit(cc_server* srv, uint32_t n, const uint32_t* row_ptr, const uint32_t* col_idx,
+                          uint64_t predicted_bytes, uint64_t* out_id);
+/* One scheduling round (see above).  Up to cap completions are written to out and their
+ * number to *n_out (completions beyond cap are kept for the next call).  *in_flight and
+ * *queued (may be NULL) receive the requests on the GPU and still waiting. */
+cc_status cc_serve_step(cc_server* srv, cc_completion* out, uint32_t cap, uint32_t* n_out, uint32_t* in_flight,
+                        uint32_t* queued);
+/* The built-in frontier-memory prediction for a graph with n vertices, m edges and maximum
+ * degree max_degree (bytes of two consecutive stored levels at the predicted peak). */
+uint64_t cc_serve_predict_bytes(uint32_t n, uint64_t m, uint32_t max_degree);
 
 /*
  * Allocation-free enumeration (the paper has no counterpart; this is a deployment aid).

@@ -112,6 +112,7 @@ SIGNATURES = {
                                          ctypes.c_uint32, _u64p]),
     "cc_batch_poll": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32, _u64p, ctypes.c_uint32,
                                        _u64p, _u64p, _dblp, ctypes.POINTER(cc_run_info)]),
+    "cc_get_trace": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_uint32, _u64p, _u64p, _u64p]),
     "cc_enumerate_noalloc": (ctypes.c_int32, [ctypes.c_uint32, _u32p, _u32p, ctypes.c_uint32, ctypes.c_void_p,
                                               _u64p, _u64p, _u64p]),
 }
@@ -335,6 +336,104 @@ class LoadedGraph:
     def close(self):
         if self.handle:
             cc_graph_free(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+def cc_get_trace(ctx, cap: int = 1 << 16):
+    """Per-step trace of the last cc_enumerate: (t_ns[steps], expanded[steps])."""
+    t = np.zeros(cap, dtype=np.uint64)
+    e = np.zeros(cap, dtype=np.uint64)
+    n = ctypes.c_uint64(0)
+    _check(load_library().cc_get_trace(ctx, cap, _p64(t), _p64(e), ctypes.byref(n)), "cc_get_trace")
+    k = min(int(n.value), cap)
+    return t[:k], e[:k]
+
+
+# ------------------------------------------------------------------ serving
+
+class cc_serve_options(ctypes.Structure):
+    _fields_ = [
+        ("slots", ctypes.c_uint32),
+        ("max_len", ctypes.c_uint32),
+        ("admit_bytes", ctypes.c_uint64),
+        ("steps_per_round", ctypes.c_uint32),
+        ("pad", ctypes.c_uint32),
+        ("reserve_paths", ctypes.c_uint64),
+    ]
+
+
+class cc_completion(ctypes.Structure):
+    _fields_ = [
+        ("id", ctypes.c_uint64),
+        ("hash", ctypes.c_uint64),
+        ("total", ctypes.c_uint64),
+        ("paths", ctypes.c_uint64),
+        ("hist", ctypes.c_uint64 * 65),
+        ("wait_us", ctypes.c_double),
+        ("latency_us", ctypes.c_double),
+    ]
+
+
+SIGNATURES.update({
+    "cc_serve_create": (ctypes.c_int32, [ctypes.c_void_p, ctypes.POINTER(cc_serve_options),
+                                         ctypes.POINTER(ctypes.c_void_p)]),
+    "cc_serve_destroy": (None, [ctypes.c_void_p]),
+    "cc_serve_submit": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_uint32, _u32p, _u32p, ctypes.c_uint64, _u64p]),
+    "cc_serve_step": (ctypes.c_int32, [ctypes.c_void_p, ctypes.POINTER(cc_completion), ctypes.c_uint32,
+                                       ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(ctypes.c_uint32),
+                                       ctypes.POINTER(ctypes.c_uint32)]),
+    "cc_serve_predict_bytes": (ctypes.c_uint64, [ctypes.c_uint32, ctypes.c_uint64, ctypes.c_uint32]),
+})
+
+
+def cc_serve_predict_bytes(n: int, m: int, max_degree: int) -> int:
+    return int(load_library().cc_serve_predict_bytes(n, m, max_degree))
+
+
+class Server:
+    """Continuous-batching request loop on a context (see cc_serve_* in include/cc.h)."""
+
+    def __init__(self, ctx: Context, slots: int = 0, max_len: int = 0, admit_bytes: int = 0,
+                 steps_per_round: int = 0, reserve_paths: int = 0, cap: int = 4096):
+        o = cc_serve_options(slots, max_len, admit_bytes, steps_per_round, 0, reserve_paths)
+        self.handle = ctypes.c_void_p()
+        _check(load_library().cc_serve_create(ctx.handle, ctypes.byref(o), ctypes.byref(self.handle)),
+               "cc_serve_create")
+        self._buf = (cc_completion * cap)()
+        self._cap = cap
+
+    def submit(self, graph, predicted_bytes: int = 0) -> int:
+        rp = np.ascontiguousarray(graph.row_ptr, dtype=np.uint32)
+        cl = np.ascontiguousarray(graph.col if graph.col.size else np.zeros(1, np.uint32), dtype=np.uint32)
+        rid = ctypes.c_uint64(0)
+        _check(load_library().cc_serve_submit(self.handle, graph.n, _p32(rp), _p32(cl), predicted_bytes,
+                                              ctypes.byref(rid)), "cc_serve_submit")
+        return int(rid.value)
+
+    def step(self):
+        """One round; returns (completions, in_flight, queued).  Each completion is a dict."""
+        n = ctypes.c_uint32(0)
+        inf = ctypes.c_uint32(0)
+        q = ctypes.c_uint32(0)
+        _check(load_library().cc_serve_step(self.handle, self._buf, self._cap, ctypes.byref(n), ctypes.byref(inf),
+                                            ctypes.byref(q)), "cc_serve_step")
+        out = []
+        for i in range(n.value):
+            c = self._buf[i]
+            out.append({"id": int(c.id), "hash": int(c.hash), "total": int(c.total), "paths": int(c.paths),
+                        "hist": np.array(c.hist[:], dtype=np.uint64), "wait_us": c.wait_us,
+                        "latency_us": c.latency_us})
+        return out, int(inf.value), int(q.value)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load_library().cc_serve_destroy(self.handle)
             self.handle = None
 
     def __enter__(self):

@@ -14,216 +14,10 @@
 #include <thread>
 #include <vector>
 
-#include "../../include/cc.h"
-#include "cc_internal.cuh"
+
+#include "cc_host.hpp"
 
 using namespace cc;
-
-namespace {
-
-constexpr unsigned int kDefaultSpin = 1u << 25;   // ~8 s of polling at 256 ns
-constexpr unsigned long long kDefaultFrontierCap = 16ull << 30;
-
-struct DevBuf {
-  void* p = nullptr;
-  size_t bytes = 0;
-};
-
-}  // namespace
-
-struct cc_context {
-  int device = 0;
-  int sms = 0;
-  cudaStream_t stream = nullptr;
-  bool own_stream = false;
-  cc_options opts{};
-  unsigned char* arena = nullptr;
-  unsigned long long arena_bytes = 0;
-  bool own_arena = false;
-  Control* ctl = nullptr;
-  Frame* frames = nullptr;
-  unsigned int frames_cap = 0;
-  // per-call result buffers (device) and their pinned host mirrors
-  unsigned long long* d_res = nullptr;  // hist | tcount | hash, grown on demand
-  size_t d_res_words = 0;
-  unsigned long long* h_res = nullptr;
-  size_t h_res_words = 0;
-  Control* h_ctl = nullptr;
-  cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev2 = nullptr, ev3 = nullptr;
-  cc_run_info last{};
-  // batch state
-  struct Batch {
-    cc_batch_id id = 0;
-    bool active = false;
-    unsigned int count = 0;
-    unsigned int max_len = 0;
-    std::vector<unsigned int> L;  // L' per graph
-    void* d_pack = nullptr;       // packed CSR + per-slot tables
-    size_t d_pack_bytes = 0;
-    unsigned long long* d_hist = nullptr;
-    unsigned long long* d_hash = nullptr;
-    unsigned long long* d_tcount = nullptr;
-    unsigned int* d_last = nullptr;
-    unsigned long long* d_ts = nullptr;
-    unsigned int ts_cap = 0;
-    cc_status status = CC_OK;
-    int grid = 0;
-  } batch;
-  cc_batch_id next_batch = 1;
-};
-
-struct cc_graph {
-  cc_context* ctx = nullptr;
-  unsigned int n = 0;
-  unsigned long long m = 0;
-  unsigned int maxdeg = 0;
-  unsigned int* d_row = nullptr;    // original CSR (sorted rows)
-  unsigned int* d_col = nullptr;
-  unsigned int* d_perm = nullptr;   // [2n]: new->orig, orig->new
-  unsigned long long* d_adj = nullptr;  // bitset rows (n <= 256), W words per row
-  int W = 0;
-  unsigned long long* d_rtab = nullptr;
-  unsigned int* d_nrow = nullptr;   // relabelled CSR
-  unsigned short* d_ncol = nullptr;
-  size_t nrow_bytes = 0, ncol_bytes = 0, adj_bytes = 0, rtab_bytes = 0;
-};
-
-// ------------------------------------------------------------------ helpers
-
-static cc_status cuda_status(cudaError_t e) {
-  if (e == cudaSuccess) return CC_OK;
-  if (e == cudaErrorMemoryAllocation) return CC_ERR_OOM;
-  return CC_ERR_CUDA;
-}
-
-#define CC_CUDA(call)                              \
-  do {                                             \
-    cudaError_t e_ = (call);                       \
-    if (e_ != cudaSuccess) {                       \
-      (void)cudaGetLastError();                    \
-      return cuda_status(e_);                      \
-    }                                              \
-  } while (0)
-
-static unsigned long long r16(unsigned long long x) { return (x + 15) & ~15ull; }
-
-static cc_status dev_alloc(cc_context* c, void** p, size_t bytes) {
-  *p = nullptr;
-  if (bytes == 0) bytes = 16;
-  CC_CUDA(cudaMallocAsync(p, bytes, c->stream));
-  return CC_OK;
-}
-static void dev_free(cc_context* c, void* p) {
-  if (p) cudaFreeAsync(p, c->stream);
-}
-
-static cc_status ensure_results(cc_context* c, size_t words) {
-  if (c->d_res_words < words) {
-    dev_free(c, c->d_res);
-    c->d_res = nullptr;
-    c->d_res_words = 0;
-    cc_status s = dev_alloc(c, (void**)&c->d_res, words * 8);
-    if (s) return s;
-    c->d_res_words = words;
-  }
-  if (c->h_res_words < words) {
-    if (c->h_res) cudaFreeHost(c->h_res);
-    c->h_res = nullptr;
-    c->h_res_words = 0;
-    CC_CUDA(cudaMallocHost((void**)&c->h_res, words * 8));
-    c->h_res_words = words;
-  }
-  return CC_OK;
-}
-
-static cc_status ensure_frames(cc_context* c, unsigned int depth) {
-  if (c->frames_cap >= depth) return CC_OK;
-  dev_free(c, c->frames);
-  c->frames = nullptr;
-  c->frames_cap = 0;
-  unsigned int cap = std::max(depth, 256u);
-  cc_status s = dev_alloc(c, (void**)&c->frames, sizeof(Frame) * cap);
-  if (s) return s;
-  c->frames_cap = cap;
-  return CC_OK;
-}
-
-static cc_status ensure_arena(cc_context* c) {
-  if (c->arena) return CC_OK;
-  if (c->opts.workspace) {
-    if ((reinterpret_cast<uintptr_t>(c->opts.workspace) & 255) || c->opts.workspace_bytes < (1u << 20))
-      return CC_ERR_ARG;
-    c->arena = static_cast<unsigned char*>(c->opts.workspace);
-    c->arena_bytes = c->opts.workspace_bytes & ~255ull;
-    c->own_arena = false;
-    return CC_OK;
-  }
-  unsigned long long want = c->opts.frontier_bytes;
-  if (want == 0) {
-    size_t fr = 0, tot = 0;
-    CC_CUDA(cudaMemGetInfo(&fr, &tot));
-    want = std::min<unsigned long long>(kDefaultFrontierCap, (unsigned long long)(fr * 0.4));
-  }
-  want &= ~255ull;
-  if (want < (1u << 16)) return CC_ERR_ARG;
-  void* p = nullptr;
-  CC_CUDA(cudaMalloc(&p, want));
-  c->arena = static_cast<unsigned char*>(p);
-  c->arena_bytes = want;
-  c->own_arena = true;
-  return CC_OK;
-}
-
-static int engine_grid(cc_context* c, Kind kind, int block, size_t smem) {
-  int bps = 0;
-  if (engine_occupancy(kind, block, smem, &bps) != cudaSuccess) {
-    (void)cudaGetLastError();
-    return 0;
-  }
-  unsigned int want = c->opts.blocks_per_sm ? c->opts.blocks_per_sm : 4u;
-  bps = std::min<int>(bps, (int)want);
-  return bps * c->sms;
-}
-
-// Validate a CSR (Section 1: finite undirected simple graph) and return sorted rows.
-static cc_status validate_csr(unsigned int n, const uint32_t* row_ptr, const uint32_t* col,
-                              std::vector<uint32_t>& sorted, unsigned int* maxdeg) {
-  if (!row_ptr) return CC_ERR_ARG;
-  if (row_ptr[0] != 0) return CC_ERR_INVALID_GRAPH;
-  for (unsigned int v = 0; v < n; ++v)
-    if (row_ptr[v + 1] < row_ptr[v]) return CC_ERR_INVALID_GRAPH;
-  const uint32_t nnz = row_ptr[n];
-  if (nnz && !col) return CC_ERR_ARG;
-  sorted.assign(col, col + nnz);
-  unsigned int md = 0;
-  for (unsigned int v = 0; v < n; ++v) {
-    auto b = sorted.begin() + row_ptr[v], e = sorted.begin() + row_ptr[v + 1];
-    std::sort(b, e);
-    for (auto it = b; it != e; ++it) {
-      if (*it >= n || *it == v) return CC_ERR_INVALID_GRAPH;
-      if (it != b && *it == *(it - 1)) return CC_ERR_INVALID_GRAPH;
-    }
-    md = std::max(md, (unsigned int)(row_ptr[v + 1] - row_ptr[v]));
-  }
-  for (unsigned int v = 0; v < n; ++v)
-    for (uint32_t e = row_ptr[v]; e < row_ptr[v + 1]; ++e) {
-      const uint32_t w = sorted[e];
-      if (!std::binary_search(sorted.begin() + row_ptr[w], sorted.begin() + row_ptr[w + 1], v))
-        return CC_ERR_INVALID_GRAPH;
-    }
-  *maxdeg = md;
-  return CC_OK;
-}
-
-static cc_status map_dev_err(int err) {
-  switch (err) {
-    case kDevOk: return CC_OK;
-    case kDevTimeout: return CC_ERR_TIMEOUT;
-    case kDevCapacity: return CC_ERR_CAPACITY;
-    case kDevSeedCap: return CC_ERR_CAPACITY;
-    default: return CC_ERR_CUDA;
-  }
-}
 
 // ------------------------------------------------------------------ context
 
@@ -276,6 +70,7 @@ extern "C" void cc_context_destroy(cc_context* c) {
   auto& b = c->batch;
   dev_free(c, b.d_pack);
   dev_free(c, c->d_res);
+  dev_free(c, c->d_trace);
   dev_free(c, c->frames);
   dev_free(c, c->ctl);
   if (c->stream) cudaStreamSynchronize(c->stream);
@@ -462,6 +257,16 @@ extern "C" cc_status cc_enumerate(cc_graph* g, uint32_t max_len, uint64_t* out_h
   p.spin_limit = c->opts.spin_limit ? c->opts.spin_limit : kDefaultSpin;
   p.fresh = 1;
   p.seed_entries = (unsigned int)(2 * g->m);
+  if (!c->d_trace) {
+    if ((s = dev_alloc(c, (void**)&c->d_trace, 16ull * kTraceCap))) {
+      free_cyc();
+      return s;
+    }
+    c->trace_cap = kTraceCap;
+  }
+  p.step_ts = c->d_trace;
+  p.step_rec = c->d_trace + c->trace_cap;
+  p.step_ts_cap = c->trace_cap;
   p.cyc_vert = d_cv;
   p.cyc_start = d_cs;
   p.cyc_len = d_cl;
@@ -495,7 +300,7 @@ extern "C" cc_status cc_enumerate(cc_graph* g, uint32_t max_len, uint64_t* out_h
     p.rtab_bytes = (unsigned int)g->rtab_bytes;
     smem = g->adj_bytes + g->rtab_bytes;
   }
-  const int block = c->opts.threads_per_block ? (int)c->opts.threads_per_block : 512;
+  const int block = c->opts.threads_per_block ? (int)c->opts.threads_per_block : 256;
   const int grid = engine_grid(c, kind, block, smem);
   if (grid <= 0) {
     free_cyc();
@@ -512,7 +317,7 @@ extern "C" cc_status cc_enumerate(cc_graph* g, uint32_t max_len, uint64_t* out_h
   ok(cudaEventRecord(c->ev0, st));
   ok(cudaMemsetAsync(c->ctl, 0, sizeof(Control), st));
   ok(cudaMemsetAsync(c->d_res, 0, words * 8, st));
-  ok(launch_label_single(g->d_row, g->d_col, n, W, g->d_perm, g->d_adj, g->d_rtab, g->d_nrow, g->d_ncol, st));
+  ok(launch_label_single(g->d_row, g->d_col, n, (unsigned int)(2 * g->m), W, g->d_perm, g->d_adj, g->d_rtab, g->d_nrow, g->d_ncol, st));
   ok(launch_seed_single(kind, p, seed_stride, st));
   ok(cudaEventRecord(c->ev3, st));
   ok(launch_engine(kind, p, grid, block, smem, st));
@@ -538,6 +343,7 @@ extern "C" cc_status cc_enumerate(cc_graph* g, uint32_t max_len, uint64_t* out_h
   *out_hash = c->h_res[2 * (L + 1)];
   info.ms_proc = ms1;
   info.ms_total = ms2;
+  c->last_t_start = h.t_start;
   info.steps = h.step;
   info.spilled = h.spilled;
   info.peak_bytes = h.peak;
@@ -577,6 +383,23 @@ extern "C" cc_status cc_enumerate(cc_graph* g, uint32_t max_len, uint64_t* out_h
   c->last = info;
   if (out_info) *out_info = info;
   return s;
+}
+
+extern "C" cc_status cc_get_trace(cc_context* c, uint32_t cap, uint64_t* t_ns, uint64_t* expanded, uint64_t* n_steps) {
+  if (!c || !n_steps || (cap && (!t_ns || !expanded))) return CC_ERR_ARG;
+  *n_steps = c->last.steps;
+  if (!c->d_trace || cap == 0) return CC_OK;
+  const unsigned long long k = std::min<unsigned long long>({(unsigned long long)cap, c->last.steps,
+                                                            (unsigned long long)c->trace_cap});
+  if (k == 0) return CC_OK;
+  if (cudaMemcpyAsync(t_ns, c->d_trace, 8 * k, cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
+      cudaMemcpyAsync(expanded, c->d_trace + c->trace_cap, 8 * k, cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
+      cudaStreamSynchronize(c->stream) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return CC_ERR_CUDA;
+  }
+  for (unsigned long long i = 0; i < k; ++i) t_ns[i] -= c->last_t_start;
+  return CC_OK;
 }
 
 // ------------------------------------------------------------------ batch
@@ -692,14 +515,14 @@ extern "C" cc_status cc_batch_submit(cc_context* c, uint32_t count, const uint32
   if (seed_bytes > c->arena_bytes / 2) return CC_ERR_CAPACITY;
   p.seed_stride = seed_stride;
   p.seed_bytes = seed_bytes;
-  const int block = c->opts.threads_per_block ? (int)c->opts.threads_per_block : 512;
+  const int block = c->opts.threads_per_block ? (int)c->opts.threads_per_block : 256;
   const int grid = engine_grid(c, Kind::Multi, block, 0);
   if (grid <= 0) return CC_ERR_CUDA;
   ok(launch_label_seed_multi(reinterpret_cast<unsigned int*>(base + o_rows),
                              reinterpret_cast<unsigned long long*>(base + o_roff),
                              reinterpret_cast<unsigned int*>(base + o_cols),
                              reinterpret_cast<unsigned long long*>(base + o_coff),
-                             reinterpret_cast<unsigned int*>(base + o_n), count, 0, max_len, p, 0, seed_stride,
+                             reinterpret_cast<unsigned int*>(base + o_n), nullptr, count, 0, max_len, p, 0, seed_stride,
                              &c->ctl->seed_count, &c->ctl->seed_next, st));
   ok(cudaEventRecord(c->ev1, st));
   ok(launch_engine(Kind::Multi, p, grid, block, 0, st));

@@ -29,8 +29,8 @@ struct StepPlan {
 struct LocalState {
   Frame cur;
   Frame child;
-  unsigned long long bot, top, chunk;
-  unsigned int depth, has_child;
+  unsigned long long bot, top, chunk, peak;
+  unsigned int depth, has_child, gen;
 };
 
 __device__ __forceinline__ Frame load_frame(const Frame* f) {
@@ -54,7 +54,10 @@ struct KindTraits {
   static constexpr int W = K == Kind::Bitset2 ? 2 : (K == Kind::Bitset4 ? 4 : 1);
   static constexpr bool multi = K == Kind::Multi;
   static constexpr bool csr = K == Kind::Csr;
-  static constexpr int P = K == Kind::Bitset4 ? 1 : 2;  // paths per thread per tile
+  // paths per thread per tile, and the minimum resident blocks per SM the register
+  // allocation must allow (two 512-thread blocks = 64 registers per thread)
+  static constexpr int P = K == Kind::Bitset4 ? 1 : (K == Kind::Bitset1 ? 3 : 2);
+  static constexpr int minB = K == Kind::Csr ? 1 : 2;
 };
 
 template <Kind K>
@@ -129,10 +132,7 @@ __device__ bool plan_step(const EngineParams& p, LocalState& st, StepPlan& pl) {
     c.next = kNoNext;
     c.t = KindTraits<K>::multi ? 0u : t + 1;
     st.has_child = 1;
-    if (blockIdx.x == 0) {
-      const unsigned long long used = p.arena_bytes - (freeb - bytes);
-      if (used > p.ctl->peak) p.ctl->peak = used;
-    }
+    st.peak = max(st.peak, p.arena_bytes - (freeb - bytes));
   }
   pl.src_base = f.base;
   pl.src_stride = f.stride;
@@ -297,12 +297,10 @@ __device__ __forceinline__ void process_bitset(const EngineParams& p, const Step
       }
     }
     if (store) {
-      unsigned int tot;
-      const unsigned int off = block_exclusive_scan(nch, &tot, s_warp);
-      if (tid == 0) *s_base = tot ? atomicAdd(&p.ctl->cnt[s % 3], (unsigned long long)tot) : 0ull;
-      __syncthreads();
-      if (tot) {
-        unsigned long long slot = *s_base + off;
+      // children slots: warp scan, then one block-wide combine and one atomic per tile
+      const unsigned long long off = tile_slots(nch, &p.ctl->cnt[s % 3], s_warp, s_base);
+      if (__any_sync(0xffffffffu, nch != 0)) {
+        unsigned long long slot = off;
 #pragma unroll
         for (int j = 0; j < P; ++j) {
           unsigned long long any = 0;
@@ -360,13 +358,11 @@ __device__ __forceinline__ void process_bitset(const EngineParams& p, const Step
       }
     }
   }
-  const unsigned long long rn = block_sum_u64(nx, s_red);
-  if (tid == 0 && rn) atomicAdd(&p.ctl->nxt[s % 3], rn);
-  if constexpr (!MULTI) {
-    const unsigned long long rc = block_sum_u64(ncyc, s_red);
-    if (tid == 0 && rc) atomicAdd(&p.hist[t + 1], rc);
-    const unsigned long long rh = block_sum_u64(hacc, s_red);
-    if (tid == 0 && rh) atomicAdd(p.hash, rh);
+  block_sum3_u64(nx, ncyc, hacc, s_red);
+  if (tid == 0) {
+    if (nx) atomicAdd(&p.ctl->nxt[s % 3], nx);
+    if (!MULTI && ncyc) atomicAdd(&p.hist[t + 1], ncyc);
+    if (!MULTI && hacc) atomicAdd(p.hash, hacc);
   }
 }
 
@@ -491,12 +487,9 @@ __device__ __forceinline__ void process_csr(const EngineParams& p, const StepPla
         }
       }
       if (store) {
-        unsigned int tot;
-        const unsigned int off = block_exclusive_scan(__popc(mask), &tot, s_warp);
-        if (tid == 0) *s_base = tot ? atomicAdd(&p.ctl->cnt[s % 3], (unsigned long long)tot) : 0ull;
-        __syncthreads();
-        if (tot) {
-          unsigned long long slot = *s_base + off;
+        const unsigned long long off = tile_slots(__popc(mask), &p.ctl->cnt[s % 3], s_warp, s_base);
+        if (mask) {
+          unsigned long long slot = off;
           while (mask) {
             const unsigned int q = __ffs(mask) - 1;
             mask &= mask - 1;
@@ -521,21 +514,21 @@ __device__ __forceinline__ void process_csr(const EngineParams& p, const StepPla
       }
     }
   }
-  const unsigned long long rc = block_sum_u64(ncyc, s_red);
-  if (threadIdx.x == 0 && rc) atomicAdd(&p.hist[t + 1], rc);
-  const unsigned long long rh = block_sum_u64(hacc, s_red);
-  if (threadIdx.x == 0 && rh) atomicAdd(p.hash, rh);
+  unsigned long long zero = 0;
+  block_sum3_u64(ncyc, hacc, zero, s_red);
+  if (threadIdx.x == 0 && ncyc) atomicAdd(&p.hist[t + 1], ncyc);
+  if (threadIdx.x == 0 && hacc) atomicAdd(p.hash, hacc);
 }
 
 // ------------------------------------------------------------------ the persistent kernel
 
 template <Kind K>
-__global__ void __launch_bounds__(kMaxThreads) engine_kernel(EngineParams p) {
+__global__ void __launch_bounds__(kMaxThreads, KindTraits<K>::minB) engine_kernel(EngineParams p) {
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ StepPlan pl;
   __shared__ LocalState st;
   __shared__ unsigned int s_warp[kMaxThreads / 32 + 1];
-  __shared__ unsigned long long s_red[kMaxThreads / 32];
+  __shared__ unsigned long long s_red[96];
   __shared__ unsigned long long s_base;
   __shared__ __align__(8) unsigned long long s_mbar;
   const unsigned int tid = threadIdx.x;
@@ -590,10 +583,8 @@ __global__ void __launch_bounds__(kMaxThreads) engine_kernel(EngineParams p) {
       st.cur.t = KindTraits<K>::multi ? 0u : 3u;
       st.cur.end = 0;
       if (blockIdx.x == 0) c->t_start = globaltimer();
-      if (blockIdx.x == 0 && n0) {
-        store_frame(&p.frames[0], st.cur);
-        if (p.seed_bytes > c->peak) c->peak = p.seed_bytes;
-      }
+      if (blockIdx.x == 0 && n0) store_frame(&p.frames[0], st.cur);
+      if (n0 && p.seed_bytes > c->peak) c->peak = p.seed_bytes;
     } else {
       st.depth = c->depth;
       st.bot = c->bot;
@@ -601,13 +592,17 @@ __global__ void __launch_bounds__(kMaxThreads) engine_kernel(EngineParams p) {
       if (st.depth) st.cur = load_frame(&p.frames[st.depth - 1]);
     }
     pl.s = c->step;
+    st.gen = ld_acquire_u32(&c->bar_gen);
+    st.peak = c->peak;
+    // an error already raised (by seeding) stops the expansion before its first step
+    if (ld_relaxed_i32(&c->err) != 0) st.depth = 0;
   }
   __syncthreads();
   unsigned long long s = pl.s;
   unsigned int steps_here = 0;
   for (;;) {
     if (tid == 0) {
-      bool go = ld_relaxed_i32(&p.ctl->err) == 0 && (p.max_steps == 0 || steps_here < p.max_steps);
+      bool go = p.max_steps == 0 || steps_here < p.max_steps;
       if (go) go = plan_step<K>(p, st, pl);
       pl.done = go ? 0u : 1u;
       pl.s = s;
@@ -626,12 +621,15 @@ __global__ void __launch_bounds__(kMaxThreads) engine_kernel(EngineParams p) {
       p.ctl->cnt[(s + 1) % 3] = 0;
       p.ctl->nxt[(s + 1) % 3] = 0;
     }
-    if (!grid_barrier(p.ctl, gridDim.x, p.spin_limit)) break;
+    if (!grid_barrier(p.ctl, gridDim.x, p.spin_limit, st.gen)) break;
     if (tid == 0) {
       const unsigned long long c = ld_relaxed_u64(&p.ctl->cnt[s % 3]);
       const unsigned long long nx = ld_relaxed_u64(&p.ctl->nxt[s % 3]);
       commit_step<K>(p, st, c, nx, blockIdx.x == 0);
-      if (blockIdx.x == 0 && p.step_ts && s < p.step_ts_cap) p.step_ts[s] = globaltimer();
+      if (blockIdx.x == 0 && p.step_ts && s < p.step_ts_cap) {
+        p.step_ts[s] = globaltimer();
+        if (p.step_rec) p.step_rec[s] = st.chunk;
+      }
     }
     ++s;
     ++steps_here;
@@ -643,6 +641,7 @@ __global__ void __launch_bounds__(kMaxThreads) engine_kernel(EngineParams p) {
     c->top = st.top;
     if (st.depth) store_frame(&p.frames[st.depth - 1], st.cur);
     c->step = s;
+    c->peak = st.peak;
   }
 }
 

@@ -65,11 +65,16 @@ struct Frame {
   unsigned int end;           // 0 = bottom stack, 1 = top stack
 };
 
+constexpr unsigned int kBarGroupSize = 16;  // blocks per first-level barrier counter
+constexpr unsigned int kBarGroupPad = 8;    // one 32-byte sector per group counter
+constexpr unsigned int kMaxBarGroups = 256;
+
 struct Control {
   unsigned long long cnt[3];  // children written in step s (index s % 3)
   unsigned long long nxt[3];  // children-of-children of step s (exact next frame size)
-  unsigned int bar_count;
-  unsigned int bar_gen;
+  unsigned int bar_count;     // groups arrived at the current grid barrier
+  unsigned int bar_gen;       // barrier generation (released by the last group)
+  unsigned int bar_group[kMaxBarGroups * kBarGroupPad];  // blocks arrived, per group
   int err;
   int err_info;
   unsigned long long step;   // global step counter (continues across launches)
@@ -108,6 +113,7 @@ struct EngineParams {
   unsigned int* last_step;         // batch: last step that expanded a path of the slot
   long long* live;                 // batch/serving: paths of the slot still in flight
   unsigned long long* step_ts;     // globaltimer at the end of each step (optional)
+  unsigned long long* step_rec;    // paths expanded in each step (optional)
   unsigned int step_ts_cap;
   unsigned int max_steps;          // stop after this many steps in this launch (0 = no limit)
   unsigned long long reserve;      // extra child capacity reserved for admissions (records)
@@ -189,16 +195,36 @@ __device__ __forceinline__ void set_err(Control* ctl, int code, int info) {
 // Grid-wide barrier for a cooperative (co-resident) launch, with a bounded wait.
 // Returns false if this block gave up waiting or any block has reported an error;
 // every block then leaves its step loop, so the kernel always terminates.
-__device__ __forceinline__ bool grid_barrier(Control* ctl, unsigned int nblocks, unsigned int spin_limit) {
+__device__ __forceinline__ unsigned int atom_add_acq_rel(unsigned int* p, unsigned int v) {
+  unsigned int old;
+  asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+  return old;
+}
+
+// Arrival is two-level: blocks arrive on their group's counter (kBarGroupSize blocks per
+// group) and the last block of each group arrives on the grid counter, so no counter sees
+// more than max(kBarGroupSize, groups) serialised atomics.  Release/acquire atomics carry
+// the step's writes from every block to every block.
+// `gen` is the barrier generation as last seen by this block's thread 0 (read once at
+// kernel start, then advanced here), which saves a round trip per barrier.
+__device__ __forceinline__ bool grid_barrier(Control* ctl, unsigned int nblocks, unsigned int spin_limit,
+                                             unsigned int& gen) {
   __shared__ int s_ok;
   __syncthreads();
   if (threadIdx.x == 0) {
     int ok = 1;
-    unsigned int gen = ld_acquire_u32(&ctl->bar_gen);
     __threadfence();
-    unsigned int arrived = atomicAdd(&ctl->bar_count, 1u);
-    if (arrived == nblocks - 1) {
-      atomicExch(&ctl->bar_count, 0u);
+    const unsigned int group = blockIdx.x / kBarGroupSize;
+    const unsigned int groups = (nblocks + kBarGroupSize - 1) / kBarGroupSize;
+    const unsigned int gsize = min(kBarGroupSize, nblocks - group * kBarGroupSize);
+    unsigned int* gc = &ctl->bar_group[group * kBarGroupPad];
+    bool last = false;
+    if (atom_add_acq_rel(gc, 1u) == gsize - 1) {
+      *gc = 0u;  // no block of this group touches it again before the release below
+      last = atom_add_acq_rel(&ctl->bar_count, 1u) == groups - 1;
+    }
+    if (last) {
+      ctl->bar_count = 0u;
       __threadfence();
       st_release_u32(&ctl->bar_gen, gen + 1);
     } else {
@@ -210,6 +236,7 @@ __device__ __forceinline__ bool grid_barrier(Control* ctl, unsigned int nblocks,
       }
     }
     if (ld_relaxed_i32(&ctl->err) != 0) ok = 0;
+    gen += 1;
     s_ok = ok;
   }
   __syncthreads();
@@ -267,6 +294,59 @@ __device__ __forceinline__ unsigned long long block_sum_u64(unsigned long long v
   return r;
 }
 
+// Output slots for one tile: each thread asks for n slots; returns the thread's first
+// slot.  Warp-level inclusive scan, one block-wide combine of the warp totals by warp 0,
+// one global atomic per tile on *counter.  Two __syncthreads; s_warp holds blockDim/32
+// words.  Safe to call again right away (each warp reads its own offset before the next
+// call's first barrier).
+__device__ __forceinline__ unsigned long long tile_slots(unsigned int n, unsigned long long* counter,
+                                                         unsigned int* s_warp, unsigned long long* s_base) {
+  const unsigned lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  unsigned int incl = n;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned int y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= (unsigned)o) incl += y;
+  }
+  if (lane == 31) s_warp[wid] = incl;
+  __syncthreads();
+  if (wid == 0) {
+    const unsigned int v = lane < nw ? s_warp[lane] : 0u;
+    unsigned int vin = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned int y = __shfl_up_sync(0xffffffffu, vin, o);
+      if (lane >= (unsigned)o) vin += y;
+    }
+    const unsigned int btot = __shfl_sync(0xffffffffu, vin, 31);
+    if (lane < nw) s_warp[lane] = vin - v;
+    if (lane == 0) *s_base = btot ? atomicAdd(counter, (unsigned long long)btot) : 0ull;
+  }
+  __syncthreads();
+  return *s_base + s_warp[wid] + (incl - n);
+}
+
+// Block-wide sums of three u64 values; results valid in thread 0.  s_red: 96 words.
+__device__ __forceinline__ void block_sum3_u64(unsigned long long& a, unsigned long long& b,
+                                               unsigned long long& c, unsigned long long* s_red) {
+  const unsigned lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  a = warp_sum_u64(a);
+  b = warp_sum_u64(b);
+  c = warp_sum_u64(c);
+  __syncthreads();
+  if (lane == 0) {
+    s_red[wid] = a;
+    s_red[32 + wid] = b;
+    s_red[64 + wid] = c;
+  }
+  __syncthreads();
+  if (wid == 0) {
+    a = warp_sum_u64(lane < nw ? s_red[lane] : 0ull);
+    b = warp_sum_u64(lane < nw ? s_red[32 + lane] : 0ull);
+    c = warp_sum_u64(lane < nw ? s_red[64 + lane] : 0ull);
+  }
+}
+
 // ---- bulk (TMA engine, non-tensor) global->shared staging with an mbarrier
 __device__ __forceinline__ unsigned int smem_addr(const void* p) {
   return (unsigned int)__cvta_generic_to_shared(p);
@@ -313,7 +393,7 @@ __host__ __device__ __forceinline__ unsigned long long csr_region_bytes(unsigned
 
 // Kernel launchers (defined in the .cu files).
 cudaError_t launch_label_single(const unsigned int* row_ptr, const unsigned int* col, unsigned int n,
-                                int W, unsigned int* perm, unsigned long long* adj,
+                                unsigned int nnz, int W, unsigned int* perm, unsigned long long* adj,
                                 unsigned long long* rtab, unsigned int* nrow, unsigned short* ncol,
                                 cudaStream_t st);
 cudaError_t launch_seed_single(Kind kind, const EngineParams& p, unsigned long long seed_stride,
@@ -324,9 +404,13 @@ cudaError_t engine_occupancy(Kind kind, int block, size_t smem, int* blocks_per_
 size_t engine_smem_bytes(Kind kind, const EngineParams& p, int block);
 cudaError_t launch_label_seed_multi(const unsigned int* row_ptr_all, const unsigned long long* row_off,
                                     const unsigned int* col_all, const unsigned long long* col_off,
-                                    const unsigned int* n_arr, unsigned int count, unsigned int slot0,
-                                    unsigned int max_len, const EngineParams& p, unsigned long long frame_base,
-                                    unsigned long long stride, unsigned long long* slot_counter,
-                                    unsigned long long* next_counter, cudaStream_t st);
+                                    const unsigned int* n_arr, const unsigned int* slot_ids, unsigned int count,
+                                    unsigned int slot0, unsigned int max_len, const EngineParams& p,
+                                    unsigned long long frame_base, unsigned long long stride,
+                                    unsigned long long* slot_counter, unsigned long long* next_counter,
+                                    cudaStream_t st);
+cudaError_t launch_serve_gather(const unsigned int* slots, unsigned int count, unsigned long long* hist,
+                                unsigned long long* tcount, unsigned long long* hash, unsigned long long* out,
+                                cudaStream_t st);
 
 }  // namespace cc

@@ -22,13 +22,24 @@ __global__ void __launch_bounds__(1024) label_single_kernel(const unsigned int* 
                                                             const unsigned int* __restrict__ col, unsigned int n,
                                                             int W, unsigned int* perm, unsigned int* newid,
                                                             unsigned long long* adj, unsigned long long* rtab,
-                                                            unsigned int* nrow, unsigned short* ncol) {
+                                                            unsigned int* nrow, unsigned short* ncol, int stage_csr) {
   extern __shared__ unsigned int sm_label[];
   unsigned int* key = sm_label;
   const unsigned int G = (n + 31) / 32;
   unsigned int* gmin = sm_label + n;
   const unsigned int tid = threadIdx.x, lane = tid & 31;
   const unsigned int kDead = 0xFFFFFFFFu;
+  if (stage_csr) {
+    // the sequential loop below reads a row per step: keep the CSR in shared memory
+    unsigned int* rp_s = gmin + G;
+    unsigned int* col_s = rp_s + n + 1;
+    const unsigned int nnz = row_ptr[n];
+    for (unsigned int i = tid; i <= n; i += blockDim.x) rp_s[i] = row_ptr[i];
+    for (unsigned int i = tid; i < nnz; i += blockDim.x) col_s[i] = col[i];
+    __syncthreads();
+    row_ptr = rp_s;
+    col = col_s;
+  }
 
   if (tid < 32) {
     for (unsigned int v = lane; v < n; v += 32) key[v] = ((row_ptr[v + 1] - row_ptr[v]) << 16) | v;
@@ -119,14 +130,17 @@ __global__ void __launch_bounds__(1024) label_single_kernel(const unsigned int* 
   }
 }
 
-cudaError_t launch_label_single(const unsigned int* row_ptr, const unsigned int* col, unsigned int n, int W,
-                                unsigned int* perm, unsigned long long* adj, unsigned long long* rtab,
-                                unsigned int* nrow, unsigned short* ncol, cudaStream_t st) {
+cudaError_t launch_label_single(const unsigned int* row_ptr, const unsigned int* col, unsigned int n,
+                                unsigned int nnz, int W, unsigned int* perm, unsigned long long* adj,
+                                unsigned long long* rtab, unsigned int* nrow, unsigned short* ncol, cudaStream_t st) {
   // perm holds 2n words: perm[0..n) new->original, perm[n..2n) original->new
   size_t smem = sizeof(unsigned int) * (n + (n + 31) / 32);
+  const size_t csr_words = (size_t)n + 1 + nnz;
+  const int stage = (smem + 4 * csr_words) <= 96 * 1024 ? 1 : 0;
+  if (stage) smem += 4 * csr_words;
   cudaError_t e = cudaFuncSetAttribute(label_single_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  label_single_kernel<<<1, 1024, smem, st>>>(row_ptr, col, n, W, perm, perm + n, adj, rtab, nrow, ncol);
+  label_single_kernel<<<1, 1024, smem, st>>>(row_ptr, col, n, W, perm, perm + n, adj, rtab, nrow, ncol, stage);
   return cudaGetLastError();
 }
 
@@ -351,16 +365,16 @@ cudaError_t launch_seed_single(Kind kind, const EngineParams& p, unsigned long l
 __global__ void __launch_bounds__(128) label_seed_multi_kernel(
     const unsigned int* __restrict__ row_ptr_all, const unsigned long long* __restrict__ row_off,
     const unsigned int* __restrict__ col_all, const unsigned long long* __restrict__ col_off,
-    const unsigned int* __restrict__ n_arr, unsigned int count, unsigned int slot0, unsigned int max_len,
-    EngineParams p, unsigned long long frame_base, unsigned long long stride, unsigned long long* slot_counter,
-    unsigned long long* next_counter) {
+    const unsigned int* __restrict__ n_arr, const unsigned int* __restrict__ slot_ids, unsigned int count,
+    unsigned int slot0, unsigned int max_len, EngineParams p, unsigned long long frame_base,
+    unsigned long long stride, unsigned long long* slot_counter, unsigned long long* next_counter) {
   __shared__ unsigned long long s_row[4][64];
   __shared__ unsigned long long s_r[4][64];
   __shared__ unsigned char s_nid[4][64];
   const unsigned int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
   const unsigned int gi = blockIdx.x * 4 + wl;
   if (gi >= count) return;
-  const unsigned int slot = slot0 + gi;
+  const unsigned int slot = slot_ids ? slot_ids[gi] : slot0 + gi;
   const unsigned int n = n_arr[gi];
   const unsigned int* rp = row_ptr_all + row_off[gi];
   const unsigned int* cl = col_all + col_off[gi];
@@ -489,14 +503,15 @@ __global__ void __launch_bounds__(128) label_seed_multi_kernel(
 
 cudaError_t launch_label_seed_multi(const unsigned int* row_ptr_all, const unsigned long long* row_off,
                                     const unsigned int* col_all, const unsigned long long* col_off,
-                                    const unsigned int* n_arr, unsigned int count, unsigned int slot0,
-                                    unsigned int max_len, const EngineParams& p, unsigned long long frame_base,
-                                    unsigned long long stride, unsigned long long* slot_counter,
-                                    unsigned long long* next_counter, cudaStream_t st) {
+                                    const unsigned int* n_arr, const unsigned int* slot_ids, unsigned int count,
+                                    unsigned int slot0, unsigned int max_len, const EngineParams& p,
+                                    unsigned long long frame_base, unsigned long long stride,
+                                    unsigned long long* slot_counter, unsigned long long* next_counter,
+                                    cudaStream_t st) {
   if (!count) return cudaSuccess;
-  label_seed_multi_kernel<<<(count + 3) / 4, 128, 0, st>>>(row_ptr_all, row_off, col_all, col_off, n_arr, count,
-                                                           slot0, max_len, p, frame_base, stride, slot_counter,
-                                                           next_counter);
+  label_seed_multi_kernel<<<(count + 3) / 4, 128, 0, st>>>(row_ptr_all, row_off, col_all, col_off, n_arr, slot_ids,
+                                                           count, slot0, max_len, p, frame_base, stride,
+                                                           slot_counter, next_counter);
   return cudaGetLastError();
 }
 

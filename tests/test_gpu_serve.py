@@ -1,0 +1,100 @@
+"""Serving (continuous batching): every result is the same alone and in the mix.
+
+Requests are submitted in waves between scheduling rounds, so requests admitted later
+run on the device side by side with requests admitted earlier; each completion must equal
+cc_enumerate on the same graph alone (bit-exact histogram, hash and stored-path count),
+and a sample is also checked against the CPU oracle."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1410_4876_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def cc():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1410_4876_gb300 import cc as _cc
+    _cc.load_library()
+    return _cc
+
+
+def _requests(count, seed):
+    return [I.make(*I.serving_request(i, seed)) for i in range(count)]
+
+
+def _serve(cc, ctx, graphs, waves=10, max_len=0, **kw):
+    results, ids = {}, {}
+    max_overlap = 0
+    admitted_while_busy = False
+    with cc.Server(ctx, max_len=max_len, **kw) as srv:
+        per = (len(graphs) + waves - 1) // waves
+        pending = 0
+        for w in range(waves):
+            for g in graphs[w * per:(w + 1) * per]:
+                ids[srv.submit(g)] = g
+                pending += 1
+            done, inflight, queued = srv.step()
+            if inflight > 1 and w > 0:
+                admitted_while_busy = True
+            max_overlap = max(max_overlap, inflight)
+            for d in done:
+                results[d["id"]] = d
+        rounds = 0
+        while len(results) < len(ids):
+            done, inflight, queued = srv.step()
+            for d in done:
+                results[d["id"]] = d
+            rounds += 1
+            assert rounds < 200000
+    return ids, results, max_overlap, admitted_while_busy
+
+
+def test_serve_equals_alone(cc):
+    graphs = _requests(160, 3)
+    with cc.Context(frontier_bytes=4 << 30) as ctx:
+        ids, results, overlap, busy = _serve(cc, ctx, graphs, waves=16, slots=64, steps_per_round=3)
+        assert overlap > 1 and busy
+        for rid, g in ids.items():
+            r = ctx.enumerate(g)
+            d = results[rid]
+            L = len(r.hist) - 1
+            assert d["hist"][:L + 1].tolist() == r.hist.tolist(), g.name
+            assert d["hash"] == r.hash and d["paths"] == r.paths and d["total"] == r.total
+    for rid, g in list(ids.items())[:25]:
+        if g.n <= 30:
+            ref = oracle.enumerate_cycles(g)
+            assert results[rid]["hash"] == ref.hash
+
+
+def test_serve_length_bound_and_small_budget(cc):
+    graphs = _requests(60, 11)
+    with cc.Context(frontier_bytes=2 << 30) as ctx:
+        # a tiny admission budget admits one request at a time when others are in flight
+        ids, results, overlap, busy = _serve(cc, ctx, graphs, waves=6, max_len=9, slots=16, admit_bytes=1 << 10)
+        for rid, g in ids.items():
+            r = ctx.enumerate(g, max_len=9)
+            assert results[rid]["hist"][:len(r.hist)].tolist() == r.hist.tolist()
+            assert results[rid]["hash"] == r.hash
+
+
+def test_serve_spills_when_frontier_is_small(cc):
+    graphs = [I.grid(8, 8), I.gnp(40, 0.2, 1), I.grid(7, 7)] + _requests(20, 5)
+    with cc.Context(frontier_bytes=24 << 20) as ctx:
+        ids, results, overlap, busy = _serve(cc, ctx, graphs, waves=3, slots=32, reserve_paths=1 << 12)
+        ref_ctx = cc.Context(frontier_bytes=2 << 30)
+        for rid, g in ids.items():
+            r = ref_ctx.enumerate(g)
+            assert results[rid]["hist"][:len(r.hist)].tolist() == r.hist.tolist(), g.name
+            assert results[rid]["hash"] == r.hash
+        ref_ctx.close()
+
+
+def test_predictor_is_monotone_in_n(cc):
+    a = cc.cc_serve_predict_bytes(20, 40, 5)
+    b = cc.cc_serve_predict_bytes(60, 120, 5)
+    assert 0 < a < b
