@@ -63,6 +63,16 @@ def _dist_init(world):
     return dist
 
 
+def max_over_ranks(value: float, dist, device=None) -> float:
+    """The largest value over all ranks (the bench times every rank and keeps the slowest)."""
+    if dist is None:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def _has_cuda():
     try:
         import torch
@@ -229,9 +239,7 @@ def run_ours(args, work, desc):
     step_ms = [a.elapsed_time(b) for a, b in ev]
     t_ms = float(sum(step_ms))
     if dist:
-        tt = torch.tensor([t_ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_ms = float(tt.item())
+        t_ms = max_over_ranks(t_ms, dist, dev)
         dist.barrier()
     value = world * cycles / (t_ms / 1000.0)
 
@@ -319,6 +327,7 @@ def run_batch(args):
         cyc, paths = int(hist.sum()), int(pth.sum())
         p50, p99 = _percentiles(done / 1000.0)
         eng_ms = info.ms_engine
+        last_info = info
     t = min(times)
     # plain per-graph launches (label + seed + expansion kernels per graph), same graphs
     loaded = [ctx.load(g) for g in graphs]
@@ -336,7 +345,8 @@ def run_batch(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
         "config": {"workload": f"{len(graphs)} graphs of the seeded batch mixture (50% G(n,p), 30% grids, "
                                "20% K_ab), all lengths", "cycles": cyc, "paths": paths},
-        "paths_expanded_per_s": paths / t, "engine_ms": eng_ms,
+        "paths_expanded_per_s": paths / t, "engine_ms": eng_ms, "spilled": int(last_info.spilled),
+        "peak_frontier_bytes": int(last_info.peak_bytes), "frontier_bytes": args.frontier_mb << 20,
         "per_graph_done_ms": {"p50": p50, "p99": p99},
         "per_graph_launches": {"value": seq_cyc / t_seq, "unit": "cycles/s", "seconds": t_seq},
         "batched_over_per_graph": (cyc / t) / (seq_cyc / t_seq),

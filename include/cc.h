@@ -75,13 +75,13 @@ typedef struct cc_graph cc_graph;
 /* Options of a context.  Zero-initialise and set what you need. */
 typedef struct cc_options {
   uint64_t frontier_bytes;     /* device bytes for chordless paths in flight; 0 = default  */
-                               /* (min(16 GiB, 40% of free memory)).  When a level would   */
+                               /* (min(64 GiB, 40% of free memory)).  When a level would   */
                                /* not fit, the expansion switches to depth-first chunks.  */
   void* stream;                /* cudaStream_t to run on; NULL = a stream the context owns */
   void* workspace;             /* optional caller-owned device buffer (>= 256-byte aligned)*/
   uint64_t workspace_bytes;    /* used as the frontier arena instead of an allocation      */
-  uint32_t threads_per_block;  /* expansion kernel block size (128..1024, multiple of 32) */
-  uint32_t blocks_per_sm;      /* persistent blocks per SM; 0 = occupancy limit (max 4)   */
+  uint32_t threads_per_block;  /* expansion kernel block size (64..256, multiple of 32; 0 = 256) */
+  uint32_t blocks_per_sm;      /* persistent blocks per SM; 0 = occupancy limit, at most 4 */
   uint32_t mode;               /* CC_MODE_*                                               */
   uint32_t spin_limit;         /* grid-barrier wait limit in polls; 0 = default (~8 s)    */
 } cc_options;

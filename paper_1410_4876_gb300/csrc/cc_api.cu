@@ -26,7 +26,7 @@ extern "C" cc_status cc_context_create(const cc_options* opts, cc_context** out)
   *out = nullptr;
   cc_options o{};
   if (opts) o = *opts;
-  if (o.threads_per_block && (o.threads_per_block < 128 || o.threads_per_block > 512 || o.threads_per_block % 32))
+  if (o.threads_per_block && (o.threads_per_block < 64 || o.threads_per_block > 256 || o.threads_per_block % 32))
     return CC_ERR_ARG;
   if (o.mode > CC_MODE_CSR) return CC_ERR_ARG;
   int dev = 0;
@@ -199,9 +199,10 @@ extern "C" cc_status cc_enumerate(cc_graph* g, uint32_t max_len, uint64_t* out_h
   Kind kind;
   const unsigned int mode = c->opts.mode;
   if (mode == CC_MODE_BITSET && (g->W == 0 || out_cycles)) return CC_ERR_UNSUPPORTED;
-  if (out_cycles || mode == CC_MODE_CSR || g->W == 0) kind = Kind::Csr;
+  if (out_cycles || mode == CC_MODE_CSR || g->W == 0)
+    kind = L <= 17 ? Kind::Csr16 : (L <= 33 ? Kind::Csr32 : Kind::Csr);  // stored paths have < L' vertices
   else kind = g->W == 1 ? Kind::Bitset1 : (g->W == 2 ? Kind::Bitset2 : Kind::Bitset4);
-  info.mode = kind == Kind::Csr ? CC_MODE_CSR : CC_MODE_BITSET;
+  info.mode = is_csr(kind) ? CC_MODE_CSR : CC_MODE_BITSET;
   if (n < 3 || L < 3) {
     if (out_info) *out_info = info;
     c->last = info;
@@ -276,7 +277,7 @@ extern "C" cc_status cc_enumerate(cc_graph* g, uint32_t max_len, uint64_t* out_h
   unsigned long long tb = g->maxdeg > 1 ? (unsigned long long)(g->maxdeg - 1) * g->m / 2 + 8 : 8;
   const unsigned long long seed_stride = round_up(tb, 8);
   const unsigned long long seed_bytes =
-      kind == Kind::Csr ? csr_region_bytes(seed_stride, 3) : bitset_region_bytes(seed_stride, W);
+      is_csr(kind) ? csr_region_bytes(seed_stride, 3) : bitset_region_bytes(seed_stride, W);
   if (seed_bytes > c->arena_bytes / 2) {
     free_cyc();
     return CC_ERR_CAPACITY;
@@ -285,7 +286,7 @@ extern "C" cc_status cc_enumerate(cc_graph* g, uint32_t max_len, uint64_t* out_h
   p.seed_bytes = seed_bytes;
   // graph staging into shared memory
   size_t smem = 0;
-  if (kind == Kind::Csr) {
+  if (is_csr(kind)) {
     const size_t need = g->nrow_bytes + g->ncol_bytes + g->rtab_bytes;
     if (need <= 160 * 1024) {
       p.smem_graph = 1;

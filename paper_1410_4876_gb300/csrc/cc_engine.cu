@@ -16,7 +16,7 @@
 
 namespace cc {
 
-constexpr int kMaxThreads = 512;
+constexpr int kMaxThreads = 256;
 
 struct StepPlan {
   unsigned long long src_base, src_stride, begin, end;
@@ -53,11 +53,12 @@ template <Kind K>
 struct KindTraits {
   static constexpr int W = K == Kind::Bitset2 ? 2 : (K == Kind::Bitset4 ? 4 : 1);
   static constexpr bool multi = K == Kind::Multi;
-  static constexpr bool csr = K == Kind::Csr;
-  // paths per thread per tile, and the minimum resident blocks per SM the register
-  // allocation must allow (two 512-thread blocks = 64 registers per thread)
+  static constexpr bool csr = is_csr(K);
+  static constexpr int cap = K == Kind::Csr16 ? 16 : (K == Kind::Csr32 ? 32 : 64);
+  // paths per thread per tile, and the minimum resident 256-thread blocks per SM the
+  // register allocation must allow (4 blocks = 64 registers per thread, 3 = 85, 2 = 128)
   static constexpr int P = K == Kind::Bitset4 ? 1 : (K == Kind::Bitset1 ? 3 : 2);
-  static constexpr int minB = K == Kind::Csr ? 1 : 2;
+  static constexpr int minB = (K == Kind::Csr || K == Kind::Csr32) ? 2 : ((K == Kind::Multi || K == Kind::Csr16) ? 3 : 4);
 };
 
 template <Kind K>
@@ -86,7 +87,8 @@ __device__ bool plan_step(const EngineParams& p, LocalState& st, StepPlan& pl) {
   const unsigned int t = f.t;
   unsigned long long need;
   if constexpr (KindTraits<K>::csr) {
-    need = (t + 1 < p.L) ? rem * p.maxch : 0ull;
+    // CSR frames carry an upper bound on their children (sum of deg(v_t) - 1)
+    need = (t + 1 < p.L) ? ((f.cursor == 0 && f.next != kNoNext) ? f.next : rem * p.maxch) : 0ull;
   } else if constexpr (KindTraits<K>::multi) {
     need = (f.cursor == 0 && f.next != kNoNext) ? f.next : rem * p.maxch;
   } else {
@@ -160,7 +162,7 @@ __device__ void commit_step(const EngineParams& p, LocalState& st, unsigned long
     Frame g = st.child;
     g.count = c;
     g.cursor = 0;
-    g.next = KindTraits<K>::csr ? kNoNext : nx;
+    g.next = nx;  // exact (bitset, batch) or an upper bound (CSR)
     if (g.end) st.top = g.base; else st.bot = g.base + g.bytes;
     if (st.depth >= p.max_depth) {
       set_err(p.ctl, kDevDepth, (int)st.depth);
@@ -178,6 +180,40 @@ __device__ void commit_step(const EngineParams& p, LocalState& st, unsigned long
 }
 
 // ------------------------------------------------------------------ bitset expansion
+
+// Batch-mode statistics of one (slot, length) key, accumulated per lane; flush() is
+// warp-collective and adds the warp's sums to the slot's histogram, hash, stored-path
+// count and in-flight count with one lane's atomics.
+struct StatRun {
+  unsigned int key;
+  unsigned int c = 0, k = 0, n = 0;
+  unsigned long long h = 0;
+  __device__ __forceinline__ void add(unsigned int cc, unsigned int kk, unsigned long long hh) {
+    c += cc;
+    k += kk;
+    n += 1;
+    h += hh;
+  }
+  __device__ __forceinline__ void flush(const EngineParams& p, unsigned long long s) {
+    const unsigned int sc = __reduce_add_sync(0xffffffffu, c);
+    const unsigned int sk = __reduce_add_sync(0xffffffffu, k);
+    const unsigned int sn = __reduce_add_sync(0xffffffffu, n);
+    const unsigned long long sh = warp_sum_u64(h);
+    if ((threadIdx.x & 31) == 0 && key != 0xFFFFFFFFu && sn) {
+      const unsigned int g = key >> 6, tt = key & 63u;
+      const unsigned long long hb = (unsigned long long)g * kMultiHistStride;
+      if (sc) atomicAdd(&p.hist[hb + tt + 1], (unsigned long long)sc);
+      if (sh) atomicAdd(&p.hash[g], sh);
+      if (sk) atomicAdd(&p.tcount[hb + tt + 1], (unsigned long long)sk);
+      if (p.live)
+        atomicAdd(reinterpret_cast<unsigned long long*>(&p.live[g]),
+                  (unsigned long long)((long long)sk - (long long)sn));
+      if (p.last_step) atomicMax(&p.last_step[g], (unsigned int)s);
+    }
+    c = k = n = 0;
+    h = 0;
+  }
+};
 
 // Algorithm 3 on bitset records.  For a path p = <v1 .. vt> with blocked set B:
 //   cand  = Adj(vt) & ~B      label test (l(v) > l(v2)), v not on p, chord test v2..v_{t-1}
@@ -207,6 +243,8 @@ __device__ __forceinline__ void process_bitset(const EngineParams& p, const Step
   const bool close_ok1 = t + 1 <= L, next_ok1 = t + 2 < L;
   unsigned long long nx = 0, ncyc = 0, hacc = 0;
   const unsigned long long tile = (unsigned long long)P * blockDim.x;
+  StatRun run;  // batch mode: the warp's current run of records with one (slot, length)
+  run.key = 0xFFFFFFFFu;
 
   for (unsigned long long t0 = pl.begin + (unsigned long long)blockIdx.x * tile; t0 < pl.end;
        t0 += (unsigned long long)gridDim.x * tile) {
@@ -270,29 +308,34 @@ __device__ __forceinline__ void process_bitset(const EngineParams& p, const Step
       }
     }
     if constexpr (MULTI) {
-      // per (slot, length) statistics, aggregated over the lanes of the warp that share them
+      // per (slot, length) statistics.  A frontier keeps each slot's paths together, so a
+      // warp accumulates a run of records with the same key in registers and only flushes
+      // (one set of atomics) when the key changes; lanes with a third key in the same
+      // record row are aggregated over the warp and flushed at once.
 #pragma unroll
       for (int j = 0; j < P; ++j) {
-        unsigned int pending = __ballot_sync(0xffffffffu, mkey[j] != 0xFFFFFFFFu);
-        while (pending) {
-          const int leader = __ffs(pending) - 1;
-          const unsigned int lk = __shfl_sync(0xffffffffu, mkey[j], leader);
-          const bool mine = mkey[j] == lk;
-          const unsigned int grp = __ballot_sync(0xffffffffu, mine);
-          const unsigned int c = __reduce_add_sync(0xffffffffu, mine ? mcyc[j] : 0u);
-          const unsigned int kk = __reduce_add_sync(0xffffffffu, mine ? mch[j] : 0u);
-          const unsigned long long h = warp_sum_u64(mine ? mh[j] : 0ull);
-          if ((int)lane == leader) {
-            const unsigned int g = lk >> 6, tt = lk & 63u;
-            const unsigned long long hb = (unsigned long long)g * kMultiHistStride;
-            if (c) atomicAdd(&p.hist[hb + tt + 1], (unsigned long long)c);
-            if (h) atomicAdd(&p.hash[g], h);
-            if (kk) atomicAdd(&p.tcount[hb + tt + 1], (unsigned long long)kk);
-            if (p.live) atomicAdd(reinterpret_cast<unsigned long long*>(&p.live[g]),
-                                  (unsigned long long)((long long)kk - (long long)__popc(grp)));
-            if (p.last_step) atomicMax(&p.last_step[g], (unsigned int)s);
+        const unsigned int key = mkey[j];
+        const bool v = key != 0xFFFFFFFFu;
+        const bool m0 = v && key == run.key;
+        if (m0) run.add(mcyc[j], mch[j], mh[j]);
+        const unsigned int rest = __ballot_sync(0xffffffffu, v && !m0);
+        if (rest) {
+          run.flush(p, s);
+          run.key = __shfl_sync(0xffffffffu, key, 31 - __clz(rest));
+          const bool m1 = v && !m0 && key == run.key;
+          if (m1) run.add(mcyc[j], mch[j], mh[j]);
+          unsigned int pending = __ballot_sync(0xffffffffu, v && !m0 && !m1);
+          while (pending) {
+            const int leader = __ffs(pending) - 1;
+            const unsigned int lk = __shfl_sync(0xffffffffu, key, leader);
+            const bool mine = key == lk;
+            const unsigned int grp = __ballot_sync(0xffffffffu, mine);
+            StatRun one;
+            one.key = lk;
+            if (mine) one.add(mcyc[j], mch[j], mh[j]);
+            one.flush(p, s);
+            pending &= ~grp;
           }
-          pending &= ~grp;
         }
       }
     }
@@ -358,6 +401,7 @@ __device__ __forceinline__ void process_bitset(const EngineParams& p, const Step
       }
     }
   }
+  if constexpr (MULTI) run.flush(p, s);
   block_sum3_u64(nx, ncyc, hacc, s_red);
   if (tid == 0) {
     if (nx) atomicAdd(&p.ctl->nxt[s % 3], nx);
@@ -415,7 +459,8 @@ __device__ __forceinline__ void process_csr(const EngineParams& p, const StepPla
   const bool store = ds != 0;
   const bool close_ok = t + 1 <= L;
   const unsigned long long s = pl.s;
-  unsigned long long ncyc = 0, hacc = 0;
+  unsigned long long ncyc = 0, hacc = 0, nbound = 0;
+  const bool bound_ok = t + 2 < L;  // children of the new paths are stored
   for (unsigned long long t0 = pl.begin + (unsigned long long)blockIdx.x * blockDim.x; t0 < pl.end;
        t0 += (unsigned long long)gridDim.x * blockDim.x) {
     const unsigned long long i = t0 + tid;
@@ -505,6 +550,7 @@ __device__ __forceinline__ void process_csr(const EngineParams& p, const StepPla
                 for (unsigned int k = 0; k < t; ++k) D[k * ds + slot] = ldcg16(S + k * ss + i);
               }
               D[(unsigned long long)t * ds + slot] = (unsigned short)v;
+              if (bound_ok) nbound += nrow[v + 1] - nrow[v] - 1;  // its candidates: Adj(v) minus v_t
             } else {
               set_err(p.ctl, kDevBounds, 2);
             }
@@ -514,8 +560,8 @@ __device__ __forceinline__ void process_csr(const EngineParams& p, const StepPla
       }
     }
   }
-  unsigned long long zero = 0;
-  block_sum3_u64(ncyc, hacc, zero, s_red);
+  block_sum3_u64(ncyc, hacc, nbound, s_red);
+  if (threadIdx.x == 0 && nbound) atomicAdd(&p.ctl->nxt[s % 3], nbound);
   if (threadIdx.x == 0 && ncyc) atomicAdd(&p.hist[t + 1], ncyc);
   if (threadIdx.x == 0 && hacc) atomicAdd(p.hash, hacc);
 }
@@ -579,7 +625,7 @@ __global__ void __launch_bounds__(kMaxThreads, KindTraits<K>::minB) engine_kerne
       st.cur.stride = p.seed_stride;
       st.cur.count = n0;
       st.cur.cursor = 0;
-      st.cur.next = KindTraits<K>::csr ? kNoNext : c->seed_next;
+      st.cur.next = c->seed_next;
       st.cur.t = KindTraits<K>::multi ? 0u : 3u;
       st.cur.end = 0;
       if (blockIdx.x == 0) c->t_start = globaltimer();
@@ -610,9 +656,10 @@ __global__ void __launch_bounds__(kMaxThreads, KindTraits<K>::minB) engine_kerne
     __syncthreads();
     if (pl.done) break;
     if constexpr (KindTraits<K>::csr) {
-      if (pl.t <= 16) process_csr<16>(p, pl, nrow, ncol, rtab, s_warp, s_red, &s_base);
-      else if (pl.t <= 32) process_csr<32>(p, pl, nrow, ncol, rtab, s_warp, s_red, &s_base);
-      else if (pl.t <= 64) process_csr<64>(p, pl, nrow, ncol, rtab, s_warp, s_red, &s_base);
+      constexpr int CAP = KindTraits<K>::cap;
+      if (CAP >= 16 && pl.t <= 16) process_csr<16>(p, pl, nrow, ncol, rtab, s_warp, s_red, &s_base);
+      else if (CAP >= 32 && pl.t <= 32) process_csr<(CAP >= 32 ? 32 : 16)>(p, pl, nrow, ncol, rtab, s_warp, s_red, &s_base);
+      else if (CAP >= 64 && pl.t <= 64) process_csr<(CAP >= 64 ? 64 : 16)>(p, pl, nrow, ncol, rtab, s_warp, s_red, &s_base);
       else process_csr<0>(p, pl, nrow, ncol, rtab, s_warp, s_red, &s_base);
     } else {
       process_bitset<K>(p, pl, adj, rtab, s_warp, s_red, &s_base);
@@ -654,6 +701,8 @@ static const void* engine_fn(Kind k) {
     case Kind::Bitset4: return (const void*)engine_kernel<Kind::Bitset4>;
     case Kind::Multi: return (const void*)engine_kernel<Kind::Multi>;
     case Kind::Csr: return (const void*)engine_kernel<Kind::Csr>;
+    case Kind::Csr16: return (const void*)engine_kernel<Kind::Csr16>;
+    case Kind::Csr32: return (const void*)engine_kernel<Kind::Csr32>;
   }
   return nullptr;
 }

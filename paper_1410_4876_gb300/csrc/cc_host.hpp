@@ -12,7 +12,7 @@ using namespace cc;
 namespace {
 
 constexpr unsigned int kDefaultSpin = 1u << 25;   // ~8 s of polling at 256 ns
-constexpr unsigned long long kDefaultFrontierCap = 16ull << 30;
+constexpr unsigned long long kDefaultFrontierCap = 64ull << 30;
 constexpr unsigned int kTraceCap = 1u << 16;  // steps recorded per call
 
 struct DevBuf {

@@ -90,7 +90,11 @@ struct Control {
   unsigned long long t_start;     // globaltimer when a fresh engine launch started
 };
 
-enum class Kind : int { Bitset1 = 0, Bitset2 = 1, Bitset4 = 2, Multi = 3, Csr = 4 };
+// Engine variants.  Csr16/Csr32 keep paths of up to 16/32 vertices in registers (chosen
+// from L'); Csr handles any length (paths up to 64 vertices in registers, longer ones
+// re-read from the frontier).
+enum class Kind : int { Bitset1 = 0, Bitset2 = 1, Bitset4 = 2, Multi = 3, Csr = 4, Csr16 = 5, Csr32 = 6 };
+__host__ __device__ constexpr bool is_csr(Kind k) { return k == Kind::Csr || k == Kind::Csr16 || k == Kind::Csr32; }
 
 struct EngineParams {
   unsigned char* arena;

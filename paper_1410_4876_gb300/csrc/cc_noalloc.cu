@@ -162,7 +162,7 @@ extern "C" cc_status cc_enumerate_noalloc(uint32_t n, const uint32_t* row_ptr, c
   p.adj_bytes = (unsigned int)round_up(8ull * npad * W, 16);
   p.rtab_bytes = (unsigned int)round_up(8ull * npad, 16);
   const size_t smem = p.adj_bytes + p.rtab_bytes;
-  const int block = 512;
+  const int block = 256;
   int bps = 0;
   if (engine_occupancy(kind, block, smem, &bps) != cudaSuccess || bps <= 0) {
     (void)cudaGetLastError();

@@ -314,6 +314,7 @@ __global__ void __launch_bounds__(256) seed_csr_kernel(EngineParams p, unsigned 
   unsigned long long base = 0;
   if (lane == 31 && wtot) base = atomicAdd(&p.ctl->seed_count, (unsigned long long)wtot);
   base = __shfl_sync(0xffffffffu, base, 31) + (incl - npath);
+  unsigned long long nb = 0;
   if (npath) {
     unsigned short* P0 = (unsigned short*)p.arena;
     unsigned long long slot = base;
@@ -324,21 +325,24 @@ __global__ void __launch_bounds__(256) seed_csr_kernel(EngineParams p, unsigned 
       P0[slot] = (unsigned short)x;
       P0[stride + slot] = (unsigned short)u;
       P0[2 * stride + slot] = (unsigned short)y;
+      if (L > 4) nb += p.nrow[y + 1] - p.nrow[y] - 1;  // bound on this path's children
       ++slot;
     }
   }
   ntri = warp_sum_u64(ntri);
   hacc = warp_sum_u64(hacc);
+  nb = warp_sum_u64(nb);
   unsigned long long np = warp_sum_u64(npath);
   if (lane == 0) {
     if (ntri) atomicAdd(&p.hist[3], ntri);
     if (hacc) atomicAdd(p.hash, hacc);
     if (np) atomicAdd(&p.tcount[3], np);
+    if (nb) atomicAdd(&p.ctl->seed_next, nb);
   }
 }
 
 cudaError_t launch_seed_single(Kind kind, const EngineParams& p, unsigned long long seed_stride, cudaStream_t st) {
-  if (kind == Kind::Csr) {
+  if (is_csr(kind)) {
     // one thread per CSR entry; row_ptr[n] is known on the host as 2m (passed via adj_bytes)
     const unsigned int m2 = p.seed_entries;
     const unsigned int blocks = (m2 + 255) / 256;
