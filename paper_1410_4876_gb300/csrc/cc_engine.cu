@@ -229,7 +229,7 @@ __device__ __forceinline__ void process_bitset(const EngineParams& p, const Step
   constexpr int W = KindTraits<K>::W;
   constexpr int P = KindTraits<K>::P;
   constexpr bool MULTI = KindTraits<K>::multi;
-  const unsigned int tid = threadIdx.x, lane = tid & 31;
+  const unsigned int tid = threadIdx.x;
   const unsigned long long ss = pl.src_stride, ds = pl.dst_stride;
   const unsigned long long* sB = reinterpret_cast<const unsigned long long*>(p.arena + pl.src_base);
   const unsigned long long* sH = sB + W * ss;
@@ -242,12 +242,17 @@ __device__ __forceinline__ void process_bitset(const EngineParams& p, const Step
   const unsigned long long s = pl.s;
   const bool close_ok1 = t + 1 <= L, next_ok1 = t + 2 < L;
   unsigned long long nx = 0, ncyc = 0, hacc = 0;
-  const unsigned long long tile = (unsigned long long)P * blockDim.x;
   StatRun run;  // batch mode: the warp's current run of records with one (slot, length)
   run.key = 0xFFFFFFFFu;
 
-  for (unsigned long long t0 = pl.begin + (unsigned long long)blockIdx.x * tile; t0 < pl.end;
-       t0 += (unsigned long long)gridDim.x * tile) {
+  // thread-interleaved grid stride: path i0 + j*T (j < P) for thread gtid, T threads in
+  // the grid, so the last round of a step is spread over every thread (no block tiles)
+  const unsigned long long T = (unsigned long long)gridDim.x * blockDim.x;
+  const unsigned long long gwarp = ((unsigned long long)blockIdx.x * blockDim.x + tid) & ~31ull;
+  // the bound is tested on the warp's first thread so every lane runs the same iterations
+  // (the body uses full-warp collectives)
+  for (unsigned long long wb = pl.begin + gwarp; wb < pl.end; wb += P * T) {
+    const unsigned long long t0 = wb + (tid & 31);
     unsigned long long B[P][W], H[P], ch[P][W];
     unsigned int M[P];
     unsigned int nch = 0;
@@ -255,7 +260,7 @@ __device__ __forceinline__ void process_bitset(const EngineParams& p, const Step
     unsigned long long mh[P];
 #pragma unroll
     for (int j = 0; j < P; ++j) {
-      const unsigned long long i = t0 + (unsigned long long)j * blockDim.x + tid;
+      const unsigned long long i = t0 + (unsigned long long)j * T;
       const bool valid = i < pl.end;
 #pragma unroll
       for (int k = 0; k < W; ++k) B[j][k] = valid ? ldcg64(sB + k * ss + i) : ~0ull;
@@ -340,8 +345,8 @@ __device__ __forceinline__ void process_bitset(const EngineParams& p, const Step
       }
     }
     if (store) {
-      // children slots: warp scan, then one block-wide combine and one atomic per tile
-      const unsigned long long off = tile_slots(nch, &p.ctl->cnt[s % 3], s_warp, s_base);
+      // children slots: warp scan and one atomic per warp (no block barrier)
+      const unsigned long long off = warp_slots(nch, &p.ctl->cnt[s % 3]);
       if (__any_sync(0xffffffffu, nch != 0)) {
         unsigned long long slot = off;
 #pragma unroll
@@ -566,6 +571,158 @@ __device__ __forceinline__ void process_csr(const EngineParams& p, const StepPla
   if (threadIdx.x == 0 && hacc) atomicAdd(p.hash, hacc);
 }
 
+// Algorithm 3 on CSR, warp-cooperative.  A warp stages its 32 paths (ids packed two per
+// word, rows padded to an odd stride) in shared memory, then works through the flattened
+// list of (path, candidate) pairs, one pair per lane per round: the pair's path comes from
+// the warp's prefix sums of candidate counts, and the tests are those of process_csr.
+// Children of a round get consecutive slots, so each plane is written contiguously.
+template <int CAP>
+__device__ __forceinline__ void process_csr_coop(const EngineParams& p, const StepPlan& pl,
+                                                 const unsigned int* nrow, const unsigned short* ncol,
+                                                 const unsigned long long* rtab) {
+  constexpr int NP = CAP / 2, RS = NP + 1;  // packed words per path, row stride (odd)
+  __shared__ unsigned int s_path[kMaxThreads / 32][32 * RS];
+  const unsigned int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  unsigned int* sp = s_path[wid];
+  const unsigned int t = pl.t, L = p.L;
+  const unsigned long long ss = pl.src_stride, ds = pl.dst_stride;
+  const unsigned short* S = reinterpret_cast<const unsigned short*>(p.arena + pl.src_base);
+  unsigned short* D = reinterpret_cast<unsigned short*>(p.arena + pl.dst_base);
+  const bool store = ds != 0;
+  const bool close_ok = t + 1 <= L, bound_ok = t + 2 < L;
+  const unsigned long long s = pl.s;
+  unsigned long long ncyc = 0, hacc = 0, nbound = 0;
+  const unsigned long long nwarps = (unsigned long long)gridDim.x * (blockDim.x >> 5);
+  for (unsigned long long w0 = pl.begin + ((unsigned long long)blockIdx.x * (blockDim.x >> 5) + wid) * 32;
+       w0 < pl.end; w0 += nwarps * 32) {
+    const unsigned long long i = w0 + lane;
+    const bool valid = i < pl.end;
+    unsigned int v1 = 0, v2 = 0xFFFFu, vt = 0, vp = 0, rb = 0, cnt = 0;
+    unsigned long long sig = 0;
+    if (valid) {
+#pragma unroll
+      for (int q = 0; q < NP; ++q) {
+        const unsigned int lo = (2u * q < t) ? ldcg16(S + (2ull * q) * ss + i) : 0xFFFFu;
+        const unsigned int hi = (2u * q + 1 < t) ? ldcg16(S + (2ull * q + 1) * ss + i) : 0xFFFFu;
+        sp[lane * RS + q] = lo | (hi << 16);
+        if (2u * q >= 1 && 2u * q + 2 <= t) sig |= 1ull << (lo & 63u);
+        if (2u * q + 3 <= t) sig |= 1ull << (hi & 63u);
+        if (q == 0) {
+          v1 = lo;
+          v2 = hi;
+        }
+      }
+      vt = ldcg16(S + (unsigned long long)(t - 1) * ss + i);
+      vp = ldcg16(S + (unsigned long long)(t - 2) * ss + i);
+      rb = nrow[vt];
+      cnt = nrow[vt + 1] - rb;
+    }
+    __syncwarp();
+    unsigned int incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned int y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= (unsigned)o) incl += y;
+    }
+    const unsigned int excl = incl - cnt, total = __shfl_sync(0xffffffffu, incl, 31);
+    for (unsigned int r0 = 0; r0 < total; r0 += 32) {
+      const unsigned int k = r0 + lane;
+      // owner: the last lane whose exclusive offset is <= k
+      unsigned int own = 0;
+#pragma unroll
+      for (int b = 16; b >= 1; b >>= 1) {
+        const unsigned int e = __shfl_sync(0xffffffffu, excl, own + b);
+        if (own + b < 32 && e <= k) own += b;
+      }
+      const unsigned int o_excl = __shfl_sync(0xffffffffu, excl, own);
+      const unsigned int o_rb = __shfl_sync(0xffffffffu, rb, own);
+      const unsigned int o_v1 = __shfl_sync(0xffffffffu, v1, own);
+      const unsigned int o_v2 = __shfl_sync(0xffffffffu, v2, own);
+      const unsigned int o_vt = __shfl_sync(0xffffffffu, vt, own);
+      const unsigned int o_vp = __shfl_sync(0xffffffffu, vp, own);
+      const unsigned long long o_sig = __shfl_sync(0xffffffffu, sig, own);
+      bool is_child = false;
+      unsigned int v = 0;
+      if (k < total) {
+        v = ncol[o_rb + (k - o_excl)];
+        if (v > o_v2 && v != o_vp) {
+          bool close = false, chord = false;
+          const unsigned int e1 = nrow[v + 1];
+          for (unsigned int e = nrow[v]; e < e1; ++e) {
+            const unsigned int w = ncol[e];
+            if (w < o_v2 || w == o_vt) continue;
+            if (w == o_v1) {
+              close = true;
+              continue;
+            }
+            if ((o_sig >> (w & 63u)) & 1ull) {
+              const unsigned int ww = w | (w << 16);
+              unsigned int any = 0;
+#pragma unroll
+              for (int q = 0; q < NP; ++q) {
+                const unsigned int x = sp[own * RS + q] ^ ww;
+                any |= (x - 0x00010001u) & ~x & 0x80008000u;
+              }
+              if (any) {
+                chord = true;
+                break;
+              }
+            }
+          }
+          if (!chord) {
+            if (close) {
+              if (close_ok) {
+                ++ncyc;
+                unsigned long long hs = rtab[v];
+#pragma unroll
+                for (int q = 0; q < NP; ++q) {
+                  const unsigned int x = sp[own * RS + q];
+                  if (2u * q < t) hs += rtab[x & 0xFFFFu];
+                  if (2u * q + 1 < t) hs += rtab[x >> 16];
+                }
+                hacc += mix64(hs + (unsigned long long)(t + 1) * kGamma);
+                if (p.cyc_vert)
+                  emit_cycle(p, t + 1, [&](unsigned int j) -> unsigned int {
+                    if (j >= t) return v;
+                    const unsigned int x = sp[own * RS + (j >> 1)];
+                    return (j & 1) ? (x >> 16) : (x & 0xFFFFu);
+                  });
+              }
+            } else {
+              is_child = store;
+            }
+          }
+        }
+      }
+      if (store) {
+        const unsigned long long slot = warp_slots(is_child ? 1u : 0u, &p.ctl->cnt[s % 3]);
+        if (is_child) {
+          if (slot < ds) {
+#pragma unroll
+            for (int q = 0; q < NP; ++q) {
+              const unsigned int x = sp[own * RS + q];
+              if (2u * q < t) D[(2ull * q) * ds + slot] = (unsigned short)(x & 0xFFFFu);
+              if (2u * q + 1 < t) D[(2ull * q + 1) * ds + slot] = (unsigned short)(x >> 16);
+            }
+            D[(unsigned long long)t * ds + slot] = (unsigned short)v;
+            if (bound_ok) nbound += nrow[v + 1] - nrow[v] - 1;  // its candidates: Adj(v) minus v_t
+          } else {
+            set_err(p.ctl, kDevBounds, 3);
+          }
+        }
+      }
+    }
+    __syncwarp();
+  }
+  __shared__ unsigned long long s_red3[96];
+  block_sum3_u64(ncyc, hacc, nbound, s_red3);
+  if (threadIdx.x == 0) {
+    if (ncyc) atomicAdd(&p.hist[t + 1], ncyc);
+    if (hacc) atomicAdd(p.hash, hacc);
+    if (nbound) atomicAdd(&p.ctl->nxt[s % 3], nbound);
+  }
+}
+
 // ------------------------------------------------------------------ the persistent kernel
 
 template <Kind K>
@@ -657,8 +814,8 @@ __global__ void __launch_bounds__(kMaxThreads, KindTraits<K>::minB) engine_kerne
     if (pl.done) break;
     if constexpr (KindTraits<K>::csr) {
       constexpr int CAP = KindTraits<K>::cap;
-      if (CAP >= 16 && pl.t <= 16) process_csr<16>(p, pl, nrow, ncol, rtab, s_warp, s_red, &s_base);
-      else if (CAP >= 32 && pl.t <= 32) process_csr<(CAP >= 32 ? 32 : 16)>(p, pl, nrow, ncol, rtab, s_warp, s_red, &s_base);
+      if (pl.t <= 16) process_csr_coop<16>(p, pl, nrow, ncol, rtab);
+      else if (CAP >= 32 && pl.t <= 32) process_csr_coop<(CAP >= 32 ? 32 : 16)>(p, pl, nrow, ncol, rtab);
       else if (CAP >= 64 && pl.t <= 64) process_csr<(CAP >= 64 ? 64 : 16)>(p, pl, nrow, ncol, rtab, s_warp, s_red, &s_base);
       else process_csr<0>(p, pl, nrow, ncol, rtab, s_warp, s_red, &s_base);
     } else {

@@ -69,14 +69,17 @@ constexpr unsigned int kBarGroupSize = 16;  // blocks per first-level barrier co
 constexpr unsigned int kBarGroupPad = 8;    // one 32-byte sector per group counter
 constexpr unsigned int kMaxBarGroups = 256;
 
+// The words that many blocks touch at once each sit on their own 128-byte line: the
+// per-step counters (atomics from every warp), the barrier generation and error word
+// (polled by waiting blocks) and the grid-level arrival counter.
 struct Control {
-  unsigned long long cnt[3];  // children written in step s (index s % 3)
-  unsigned long long nxt[3];  // children-of-children of step s (exact next frame size)
-  unsigned int bar_count;     // groups arrived at the current grid barrier
-  unsigned int bar_gen;       // barrier generation (released by the last group)
-  unsigned int bar_group[kMaxBarGroups * kBarGroupPad];  // blocks arrived, per group
-  int err;
+  alignas(128) unsigned long long cnt[3];  // children written in step s (index s % 3)
+  unsigned long long nxt[3];               // children-of-children of step s (next frame size)
+  alignas(128) unsigned int bar_gen;       // barrier generation (released by the last group)
+  int err;                                 // first device error (kDev*), 0 if none
   int err_info;
+  alignas(128) unsigned int bar_count;     // groups arrived at the current grid barrier
+  alignas(128) unsigned int bar_group[kMaxBarGroups * kBarGroupPad];  // blocks arrived, per group
   unsigned long long step;   // global step counter (continues across launches)
   unsigned long long bot;    // bottom stack top (bytes)
   unsigned long long top;    // top stack bottom (bytes)
@@ -233,10 +236,12 @@ __device__ __forceinline__ bool grid_barrier(Control* ctl, unsigned int nblocks,
       st_release_u32(&ctl->bar_gen, gen + 1);
     } else {
       unsigned int polls = 0;
+      // poll tightly for short steps, then back off so that waiting blocks do not load
+      // the memory system the working blocks need (long steps take milliseconds)
       while (ld_acquire_u32(&ctl->bar_gen) == gen) {
-        if (ld_relaxed_i32(&ctl->err) != 0) { ok = 0; break; }
+        if ((polls & 15) == 0 && ld_relaxed_i32(&ctl->err) != 0) { ok = 0; break; }
         if (++polls > spin_limit) { set_err(ctl, kDevTimeout, 1); ok = 0; break; }
-        if (polls > 32) __nanosleep(polls > 4096 ? 256 : 32);
+        if (polls > 16) __nanosleep(polls < 256 ? 64 : 512);
       }
     }
     if (ld_relaxed_i32(&ctl->err) != 0) ok = 0;
@@ -328,6 +333,23 @@ __device__ __forceinline__ unsigned long long tile_slots(unsigned int n, unsigne
   }
   __syncthreads();
   return *s_base + s_warp[wid] + (incl - n);
+}
+
+// Output slots for one warp: each lane asks for n slots; returns the lane's first slot.
+// Warp-level inclusive scan and one global atomic per warp, no block barrier, so warps of
+// a block never wait for each other.
+__device__ __forceinline__ unsigned long long warp_slots(unsigned int n, unsigned long long* counter) {
+  const unsigned lane = threadIdx.x & 31;
+  unsigned int incl = n;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned int y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= (unsigned)o) incl += y;
+  }
+  const unsigned int tot = __shfl_sync(0xffffffffu, incl, 31);
+  unsigned long long base = 0;
+  if (lane == 31 && tot) base = atomicAdd(counter, (unsigned long long)tot);
+  return __shfl_sync(0xffffffffu, base, 31) + (incl - n);
 }
 
 // Block-wide sums of three u64 values; results valid in thread 0.  s_red: 96 words.

@@ -130,9 +130,76 @@ __global__ void __launch_bounds__(1024) label_single_kernel(const unsigned int* 
   }
 }
 
+// The same labelling for n <= 64 with one-word rows: one warp, every vertex's adjacency
+// row and current degree in registers (lane l owns vertices l and l + 32), one warp
+// reduction per step and no shared or global memory inside the sequential loop.
+__global__ void __launch_bounds__(32) label_small_kernel(const unsigned int* __restrict__ row_ptr,
+                                                         const unsigned int* __restrict__ col, unsigned int n,
+                                                         unsigned int* perm, unsigned int* newid,
+                                                         unsigned long long* adj, unsigned long long* rtab) {
+  __shared__ unsigned char s_nid[64];
+  const unsigned int lane = threadIdx.x;
+  unsigned long long ao[2] = {0, 0};
+  unsigned int deg[2] = {0, 0};
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    const unsigned int v = lane + 32u * k;
+    if (v < n) {
+      for (unsigned int e = row_ptr[v]; e < row_ptr[v + 1]; ++e) ao[k] |= 1ull << col[e];
+      deg[k] = row_ptr[v + 1] - row_ptr[v];
+    }
+  }
+  unsigned long long alive = n >= 64 ? ~0ull : ((1ull << n) - 1ull);
+  for (unsigned int i = 0; i < n; ++i) {
+    unsigned int key = 0xFFFFFFFFu;
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      const unsigned int v = lane + 32u * k;
+      if (v < n && ((alive >> v) & 1ull)) key = min(key, (deg[k] << 8) | v);
+    }
+    key = __reduce_min_sync(0xffffffffu, key);
+    const unsigned int u = key & 0xFFu;
+    if (lane == 0) {
+      s_nid[u] = (unsigned char)i;
+      perm[i] = u;
+      newid[u] = i;
+    }
+    alive &= ~(1ull << u);
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      const unsigned int v = lane + 32u * k;
+      if (v < n && ((alive >> v) & 1ull) && ((ao[k] >> u) & 1ull)) deg[k] -= 1;
+    }
+  }
+  __syncwarp();
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    const unsigned int v = lane + 32u * k;
+    if (v < n) {
+      unsigned long long row = 0, b = ao[k];
+      while (b) {
+        const unsigned int w = __ffsll((long long)b) - 1;
+        b &= b - 1;
+        row |= 1ull << s_nid[w];
+      }
+      adj[s_nid[v]] = row;
+      rtab[s_nid[v]] = vertex_r(v);
+    }
+  }
+  // 16-byte padding of the staged copies
+  if (lane == 0 && (n & 1)) {
+    adj[n] = 0;
+    rtab[n] = 0;
+  }
+}
+
 cudaError_t launch_label_single(const unsigned int* row_ptr, const unsigned int* col, unsigned int n,
                                 unsigned int nnz, int W, unsigned int* perm, unsigned long long* adj,
                                 unsigned long long* rtab, unsigned int* nrow, unsigned short* ncol, cudaStream_t st) {
+  if (W == 1 && n <= 64) {
+    label_small_kernel<<<1, 32, 0, st>>>(row_ptr, col, n, perm, perm + n, adj, rtab);
+    return cudaGetLastError();
+  }
   // perm holds 2n words: perm[0..n) new->original, perm[n..2n) original->new
   size_t smem = sizeof(unsigned int) * (n + (n + 31) / 32);
   const size_t csr_words = (size_t)n + 1 + nnz;
