@@ -41,11 +41,13 @@ WORKLOADS = {
 def algorithmic_bytes(r) -> int:
     """Bytes the expansion kernel must move: every stored path is read once and every
     path after the initial triplets is written once.  Record sizes: bitset, n <= 64:
-    B (8) + H (8) + M (4) = 20 bytes; n <= 128: 28; n <= 256: 44; CSR: 2 bytes per vertex."""
+    B (8) + H (8) + M (4) = 20 bytes; n <= 128: 28; n <= 256: 44; CSR: the path's u16 ids
+    padded to a multiple of 8 (16 bytes for t <= 8, 32 for t <= 16, ...)."""
     tc = r.tcount
     if r.info.mode == 2:
-        per = np.arange(tc.size, dtype=np.int64) * 2
-        return int((tc.astype(np.int64) * per).sum() * 2 - int(tc[3]) * 6) if tc.size > 3 else 0
+        t = np.arange(tc.size, dtype=np.int64)
+        rec = (t + 7) // 8 * 16
+        return int((tc.astype(np.int64) * rec).sum() * 2 - int(tc[3]) * 16) if tc.size > 3 else 0
     n = len(r.hist) - 1
     rec = 20 if n <= 64 else (28 if n <= 128 else 44)
     return rec * (2 * int(tc.sum()) - int(tc[3]))
@@ -270,7 +272,7 @@ def run_ours(args, work, desc):
 
     peak, peak_kind = _peaks()
     achieved = eng_bytes / (eng_ms / 1000.0) / 1e9 if eng_ms > 0 else 0.0
-    traffic = _ncu_traffic()
+    traffic = _ncu_traffic(args.workload)
     line = {
         "metric": "chordless cycles/s", "value": value, "unit": "cycles/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -424,14 +426,24 @@ def run_serve(args):
     print(json.dumps(line), flush=True)
 
 
-def _ncu_traffic():
-    """DRAM bytes per launch of the expansion kernel from the committed ncu summary, when
-    the summary was taken on the current kernel (the summary records it); else None."""
-    p = os.path.join(ROOT, "profiles", "engine_bitset1_grid8_gnp60.json")
-    if not os.path.exists(p):
+def _engine_fingerprint() -> str:
+    import hashlib
+    csrc = os.path.join(ROOT, "paper_1410_4876_gb300", "csrc")
+    data = open(os.path.join(csrc, "cc_engine.cu"), "rb").read() + open(os.path.join(csrc, "cc_internal.cuh"), "rb").read()
+    return hashlib.sha256(data).hexdigest()[:16]
+
+
+def _ncu_traffic(workload: str):
+    """DRAM bytes per step of the expansion kernel from the committed ncu summary, only
+    when that summary was captured on this workload and on the current engine source
+    (its fingerprint matches); otherwise None."""
+    if workload != "grid8+gnp60":
         return None
+    p = os.path.join(ROOT, "profiles", "engine_bitset1_grid8_gnp60.json")
     try:
         d = json.load(open(p))
+        if d.get("source_fingerprint") != _engine_fingerprint():
+            return None
         return d.get("dram_bytes_per_step")
     except Exception:
         return None

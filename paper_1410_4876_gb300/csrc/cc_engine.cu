@@ -68,7 +68,7 @@ __device__ __forceinline__ unsigned long long region_bytes(unsigned long long st
 }
 template <Kind K>
 __device__ __forceinline__ unsigned long long record_bytes(unsigned int t_child) {
-  if constexpr (KindTraits<K>::csr) return 2ull * t_child;
+  if constexpr (KindTraits<K>::csr) return 2ull * csr_rec_u16(t_child);
   else return 8ull * KindTraits<K>::W + 12ull;
 }
 
@@ -417,31 +417,12 @@ __device__ __forceinline__ void process_bitset(const EngineParams& p, const Step
 
 // ------------------------------------------------------------------ CSR expansion
 
-// Path held in registers as CAP u16 ids packed two per word (unused slots 0xFFFF, never
-// a vertex id).  CAP = 0: the path is re-read from its planes (long paths).
-template <int CAP>
-struct PathRegs {
-  static constexpr int NP = CAP > 0 ? CAP / 2 : 1;
-  unsigned int pk[NP];
-};
-
-template <int CAP>
-__device__ __forceinline__ bool on_path(const PathRegs<CAP>& r, unsigned int w, const unsigned short* S,
-                                        unsigned long long ss, unsigned long long i, unsigned int t) {
-  if constexpr (CAP > 0) {
-    const unsigned int ww = w | (w << 16);
-    unsigned int any = 0;
-#pragma unroll
-    for (int q = 0; q < PathRegs<CAP>::NP; ++q) {
-      const unsigned int x = r.pk[q] ^ ww;  // a zero 16-bit lane marks an equal id
-      any |= (x - 0x00010001u) & ~x & 0x80008000u;
-    }
-    return any != 0;
-  } else {
-    for (unsigned int k = 1; k + 1 < t; ++k)
-      if (ldcg16(S + k * ss + i) == w) return true;
-    return false;
-  }
+// CSR records: the path's relabelled ids in order, as u16, padded with 0xFFFF (never a
+// vertex id) to csr_rec_u16(t) = a multiple of 8 entries, so a record is read and written
+// with 16-byte vector accesses.
+__device__ __forceinline__ unsigned int rec_id(const unsigned int* row, unsigned int k) {
+  const unsigned int x = row[k >> 1];
+  return (k & 1) ? (x >> 16) : (x & 0xFFFFu);
 }
 
 // Algorithm 3 on CSR with the path as a vertex list.  Candidate v of Adj(vt):
@@ -450,144 +431,26 @@ __device__ __forceinline__ bool on_path(const PathRegs<CAP>& r, unsigned int w, 
 //   chord test   no w in Adj(v) lies on v2..v_{t-1} (a 64-bit signature of the interior
 //                filters most w before the exact comparison);
 //   close test   v1 in Adj(v) gives a cycle of t+1 vertices, otherwise a child path.
-template <int CAP>
-__device__ __forceinline__ void process_csr(const EngineParams& p, const StepPlan& pl, const unsigned int* nrow,
-                                            const unsigned short* ncol, const unsigned long long* rtab,
-                                            unsigned int* s_warp, unsigned long long* s_red,
-                                            unsigned long long* s_base) {
-  constexpr int NP = PathRegs<CAP>::NP;
-  const unsigned int tid = threadIdx.x;
-  const unsigned int t = pl.t, L = p.L;
-  const unsigned long long ss = pl.src_stride, ds = pl.dst_stride;
-  const unsigned short* S = reinterpret_cast<const unsigned short*>(p.arena + pl.src_base);
-  unsigned short* D = reinterpret_cast<unsigned short*>(p.arena + pl.dst_base);
-  const bool store = ds != 0;
-  const bool close_ok = t + 1 <= L;
-  const unsigned long long s = pl.s;
-  unsigned long long ncyc = 0, hacc = 0, nbound = 0;
-  const bool bound_ok = t + 2 < L;  // children of the new paths are stored
-  for (unsigned long long t0 = pl.begin + (unsigned long long)blockIdx.x * blockDim.x; t0 < pl.end;
-       t0 += (unsigned long long)gridDim.x * blockDim.x) {
-    const unsigned long long i = t0 + tid;
-    const bool valid = i < pl.end;
-    PathRegs<CAP> r;
-    unsigned int v1 = 0xFFFFu, v2 = 0xFFFFu, vt = 0, vp = 0, rb = 0, deg = 0;
-    unsigned long long sig = 0;
-    if (valid) {
-      if constexpr (CAP > 0) {
-#pragma unroll
-        for (int q = 0; q < NP; ++q) {
-          const unsigned int lo = (2u * q < t) ? ldcg16(S + (2ull * q) * ss + i) : 0xFFFFu;
-          const unsigned int hi = (2u * q + 1 < t) ? ldcg16(S + (2ull * q + 1) * ss + i) : 0xFFFFu;
-          r.pk[q] = lo | (hi << 16);
-          if (2u * q >= 1 && 2u * q + 2 <= t) sig |= 1ull << (lo & 63u);
-          if (2u * q + 1 >= 1 && 2u * q + 3 <= t) sig |= 1ull << (hi & 63u);
-        }
-        v1 = r.pk[0] & 0xFFFFu;
-        v2 = r.pk[0] >> 16;
-      } else {
-        r.pk[0] = 0;
-        v1 = ldcg16(S + i);
-        v2 = ldcg16(S + ss + i);
-        for (unsigned int k = 1; k + 1 < t; ++k) sig |= 1ull << (ldcg16(S + k * ss + i) & 63u);
-      }
-      vt = ldcg16(S + (unsigned long long)(t - 1) * ss + i);
-      vp = ldcg16(S + (unsigned long long)(t - 2) * ss + i);
-      rb = nrow[vt];
-      deg = nrow[vt + 1] - rb;
-    }
-    for (unsigned int w0 = 0; __syncthreads_or(valid && w0 < deg); w0 += 32) {
-      unsigned int mask = 0;
-      if (valid && w0 < deg) {
-        const unsigned int qend = min(deg, w0 + 32);
-        for (unsigned int q = w0; q < qend; ++q) {
-          const unsigned int v = ncol[rb + q];
-          if (v <= v2 || v == vp) continue;
-          bool close = false, chord = false;
-          const unsigned int e1 = nrow[v + 1];
-          for (unsigned int e = nrow[v]; e < e1; ++e) {
-            const unsigned int w = ncol[e];
-            if (w < v2 || w == vt) continue;
-            if (w == v1) { close = true; continue; }
-            if (((sig >> (w & 63u)) & 1ull) && on_path<CAP>(r, w, S, ss, i, t)) { chord = true; break; }
-          }
-          if (chord) continue;
-          if (close) {
-            if (close_ok) {
-              ++ncyc;
-              unsigned long long hs = rtab[v];
-              if constexpr (CAP > 0) {
-#pragma unroll
-                for (int q = 0; q < NP; ++q) {
-                  if (2u * q < t) hs += rtab[r.pk[q] & 0xFFFFu];
-                  if (2u * q + 1 < t) hs += rtab[r.pk[q] >> 16];
-                }
-              } else {
-                for (unsigned int k = 0; k < t; ++k) hs += rtab[ldcg16(S + k * ss + i)];
-              }
-              hacc += mix64(hs + (unsigned long long)(t + 1) * kGamma);
-              if (p.cyc_vert)
-                emit_cycle(p, t + 1, [&](unsigned int j) -> unsigned int {
-                  return j < t ? (unsigned int)ldcg16(S + (unsigned long long)j * ss + i) : v;
-                });
-            }
-          } else if (store) {
-            mask |= 1u << (q - w0);
-          }
-        }
-      }
-      if (store) {
-        const unsigned long long off = tile_slots(__popc(mask), &p.ctl->cnt[s % 3], s_warp, s_base);
-        if (mask) {
-          unsigned long long slot = off;
-          while (mask) {
-            const unsigned int q = __ffs(mask) - 1;
-            mask &= mask - 1;
-            const unsigned int v = ncol[rb + w0 + q];
-            if (slot < ds) {
-              if constexpr (CAP > 0) {
-#pragma unroll
-                for (int qq = 0; qq < NP; ++qq) {
-                  if (2u * qq < t) D[(2ull * qq) * ds + slot] = (unsigned short)(r.pk[qq] & 0xFFFFu);
-                  if (2u * qq + 1 < t) D[(2ull * qq + 1) * ds + slot] = (unsigned short)(r.pk[qq] >> 16);
-                }
-              } else {
-                for (unsigned int k = 0; k < t; ++k) D[k * ds + slot] = ldcg16(S + k * ss + i);
-              }
-              D[(unsigned long long)t * ds + slot] = (unsigned short)v;
-              if (bound_ok) nbound += nrow[v + 1] - nrow[v] - 1;  // its candidates: Adj(v) minus v_t
-            } else {
-              set_err(p.ctl, kDevBounds, 2);
-            }
-            ++slot;
-          }
-        }
-      }
-    }
-  }
-  block_sum3_u64(ncyc, hacc, nbound, s_red);
-  if (threadIdx.x == 0 && nbound) atomicAdd(&p.ctl->nxt[s % 3], nbound);
-  if (threadIdx.x == 0 && ncyc) atomicAdd(&p.hist[t + 1], ncyc);
-  if (threadIdx.x == 0 && hacc) atomicAdd(p.hash, hacc);
-}
-
-// Algorithm 3 on CSR, warp-cooperative.  A warp stages its 32 paths (ids packed two per
-// word, rows padded to an odd stride) in shared memory, then works through the flattened
-// list of (path, candidate) pairs, one pair per lane per round: the pair's path comes from
-// the warp's prefix sums of candidate counts, and the tests are those of process_csr.
-// Children of a round get consecutive slots, so each plane is written contiguously.
+//
+// Warp-cooperative: a warp stages its 32 paths (rows of packed id pairs, odd stride) in
+// shared memory, then works through the flattened list of (path, candidate) pairs, one
+// pair per lane per round; the pair's path comes from the warp's prefix sums of candidate
+// counts.  Children of a round get consecutive slots, so their records are written
+// contiguously.  CAP bounds the staged path length (16 or 32 vertices).
 template <int CAP>
 __device__ __forceinline__ void process_csr_coop(const EngineParams& p, const StepPlan& pl,
                                                  const unsigned int* nrow, const unsigned short* ncol,
                                                  const unsigned long long* rtab) {
-  constexpr int NP = CAP / 2, RS = NP + 1;  // packed words per path, row stride (odd)
+  constexpr int NP = CAP / 2, RS = NP + 1;  // packed words per row, row stride (odd)
   __shared__ unsigned int s_path[kMaxThreads / 32][32 * RS];
   const unsigned int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   unsigned int* sp = s_path[wid];
   const unsigned int t = pl.t, L = p.L;
-  const unsigned long long ss = pl.src_stride, ds = pl.dst_stride;
-  const unsigned short* S = reinterpret_cast<const unsigned short*>(p.arena + pl.src_base);
-  unsigned short* D = reinterpret_cast<unsigned short*>(p.arena + pl.dst_base);
+  const unsigned int nv = csr_rec_u16(t) / 8, nv2 = csr_rec_u16(t + 1) / 8;  // uint4 per record
+  const unsigned int nw = (t + 1) / 2;                                         // words holding ids
+  const uint4* S = reinterpret_cast<const uint4*>(p.arena + pl.src_base);
+  uint4* D = reinterpret_cast<uint4*>(p.arena + pl.dst_base);
+  const unsigned long long ds = pl.dst_stride;
   const bool store = ds != 0;
   const bool close_ok = t + 1 <= L, bound_ok = t + 2 < L;
   const unsigned long long s = pl.s;
@@ -597,23 +460,24 @@ __device__ __forceinline__ void process_csr_coop(const EngineParams& p, const St
        w0 < pl.end; w0 += nwarps * 32) {
     const unsigned long long i = w0 + lane;
     const bool valid = i < pl.end;
+    unsigned int* row = sp + lane * RS;
     unsigned int v1 = 0, v2 = 0xFFFFu, vt = 0, vp = 0, rb = 0, cnt = 0;
     unsigned long long sig = 0;
     if (valid) {
 #pragma unroll
-      for (int q = 0; q < NP; ++q) {
-        const unsigned int lo = (2u * q < t) ? ldcg16(S + (2ull * q) * ss + i) : 0xFFFFu;
-        const unsigned int hi = (2u * q + 1 < t) ? ldcg16(S + (2ull * q + 1) * ss + i) : 0xFFFFu;
-        sp[lane * RS + q] = lo | (hi << 16);
-        if (2u * q >= 1 && 2u * q + 2 <= t) sig |= 1ull << (lo & 63u);
-        if (2u * q + 3 <= t) sig |= 1ull << (hi & 63u);
-        if (q == 0) {
-          v1 = lo;
-          v2 = hi;
-        }
+      for (int q = 0; q < CAP / 8; ++q) {
+        uint4 x = make_uint4(0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu);
+        if ((unsigned)q < nv) x = __ldcg(S + i * nv + q);
+        row[4 * q] = x.x;
+        row[4 * q + 1] = x.y;
+        row[4 * q + 2] = x.z;
+        row[4 * q + 3] = x.w;
       }
-      vt = ldcg16(S + (unsigned long long)(t - 1) * ss + i);
-      vp = ldcg16(S + (unsigned long long)(t - 2) * ss + i);
+      v1 = row[0] & 0xFFFFu;
+      v2 = row[0] >> 16;
+      vt = rec_id(row, t - 1);
+      vp = rec_id(row, t - 2);
+      for (unsigned int k = 1; k + 1 < t; ++k) sig |= 1ull << (rec_id(row, k) & 63u);
       rb = nrow[vt];
       cnt = nrow[vt + 1] - rb;
     }
@@ -631,7 +495,7 @@ __device__ __forceinline__ void process_csr_coop(const EngineParams& p, const St
       unsigned int own = 0;
 #pragma unroll
       for (int b = 16; b >= 1; b >>= 1) {
-        const unsigned int e = __shfl_sync(0xffffffffu, excl, own + b);
+        const unsigned int e = __shfl_sync(0xffffffffu, excl, (own + b) & 31);
         if (own + b < 32 && e <= k) own += b;
       }
       const unsigned int o_excl = __shfl_sync(0xffffffffu, excl, own);
@@ -641,6 +505,7 @@ __device__ __forceinline__ void process_csr_coop(const EngineParams& p, const St
       const unsigned int o_vt = __shfl_sync(0xffffffffu, vt, own);
       const unsigned int o_vp = __shfl_sync(0xffffffffu, vp, own);
       const unsigned long long o_sig = __shfl_sync(0xffffffffu, sig, own);
+      const unsigned int* orow = sp + own * RS;
       bool is_child = false;
       unsigned int v = 0;
       if (k < total) {
@@ -658,9 +523,8 @@ __device__ __forceinline__ void process_csr_coop(const EngineParams& p, const St
             if ((o_sig >> (w & 63u)) & 1ull) {
               const unsigned int ww = w | (w << 16);
               unsigned int any = 0;
-#pragma unroll
-              for (int q = 0; q < NP; ++q) {
-                const unsigned int x = sp[own * RS + q] ^ ww;
+              for (unsigned int q = 0; q < nw; ++q) {
+                const unsigned int x = orow[q] ^ ww;  // a zero 16-bit lane marks an equal id
                 any |= (x - 0x00010001u) & ~x & 0x80008000u;
               }
               if (any) {
@@ -674,19 +538,10 @@ __device__ __forceinline__ void process_csr_coop(const EngineParams& p, const St
               if (close_ok) {
                 ++ncyc;
                 unsigned long long hs = rtab[v];
-#pragma unroll
-                for (int q = 0; q < NP; ++q) {
-                  const unsigned int x = sp[own * RS + q];
-                  if (2u * q < t) hs += rtab[x & 0xFFFFu];
-                  if (2u * q + 1 < t) hs += rtab[x >> 16];
-                }
+                for (unsigned int j = 0; j < t; ++j) hs += rtab[rec_id(orow, j)];
                 hacc += mix64(hs + (unsigned long long)(t + 1) * kGamma);
                 if (p.cyc_vert)
-                  emit_cycle(p, t + 1, [&](unsigned int j) -> unsigned int {
-                    if (j >= t) return v;
-                    const unsigned int x = sp[own * RS + (j >> 1)];
-                    return (j & 1) ? (x >> 16) : (x & 0xFFFFu);
-                  });
+                  emit_cycle(p, t + 1, [&](unsigned int j) -> unsigned int { return j < t ? rec_id(orow, j) : v; });
               }
             } else {
               is_child = store;
@@ -698,13 +553,18 @@ __device__ __forceinline__ void process_csr_coop(const EngineParams& p, const St
         const unsigned long long slot = warp_slots(is_child ? 1u : 0u, &p.ctl->cnt[s % 3]);
         if (is_child) {
           if (slot < ds) {
+            const unsigned int tw = t >> 1, sh = (t & 1) * 16;
+            for (unsigned int q = 0; q < nv2; ++q) {
+              unsigned int w4[4];
 #pragma unroll
-            for (int q = 0; q < NP; ++q) {
-              const unsigned int x = sp[own * RS + q];
-              if (2u * q < t) D[(2ull * q) * ds + slot] = (unsigned short)(x & 0xFFFFu);
-              if (2u * q + 1 < t) D[(2ull * q + 1) * ds + slot] = (unsigned short)(x >> 16);
+              for (int c = 0; c < 4; ++c) {
+                const unsigned int wi = 4 * q + c;
+                unsigned int x = wi < (unsigned)NP ? orow[wi] : 0xFFFFFFFFu;
+                if (wi == tw) x = (x & ~(0xFFFFu << sh)) | (v << sh);
+                w4[c] = x;
+              }
+              D[slot * nv2 + q] = make_uint4(w4[0], w4[1], w4[2], w4[3]);
             }
-            D[(unsigned long long)t * ds + slot] = (unsigned short)v;
             if (bound_ok) nbound += nrow[v + 1] - nrow[v] - 1;  // its candidates: Adj(v) minus v_t
           } else {
             set_err(p.ctl, kDevBounds, 3);
@@ -716,6 +576,110 @@ __device__ __forceinline__ void process_csr_coop(const EngineParams& p, const St
   }
   __shared__ unsigned long long s_red3[96];
   block_sum3_u64(ncyc, hacc, nbound, s_red3);
+  if (threadIdx.x == 0) {
+    if (ncyc) atomicAdd(&p.hist[t + 1], ncyc);
+    if (hacc) atomicAdd(p.hash, hacc);
+    if (nbound) atomicAdd(&p.ctl->nxt[s % 3], nbound);
+  }
+}
+
+// The same expansion for paths longer than 32 vertices, one thread per path, the path
+// read from its record in the frontier each time it is needed (long chordless paths are
+// rare and their frames small).
+__device__ __forceinline__ void process_csr_long(const EngineParams& p, const StepPlan& pl, const unsigned int* nrow,
+                                                 const unsigned short* ncol, const unsigned long long* rtab,
+                                                 unsigned int* s_warp, unsigned long long* s_red,
+                                                 unsigned long long* s_base) {
+  const unsigned int tid = threadIdx.x;
+  const unsigned int t = pl.t, L = p.L;
+  const unsigned int R = csr_rec_u16(t), R2 = csr_rec_u16(t + 1);
+  const unsigned short* S = reinterpret_cast<const unsigned short*>(p.arena + pl.src_base);
+  unsigned short* D = reinterpret_cast<unsigned short*>(p.arena + pl.dst_base);
+  const unsigned long long ds = pl.dst_stride;
+  const bool store = ds != 0;
+  const bool close_ok = t + 1 <= L, bound_ok = t + 2 < L;
+  const unsigned long long s = pl.s;
+  unsigned long long ncyc = 0, hacc = 0, nbound = 0;
+  for (unsigned long long t0 = pl.begin + (unsigned long long)blockIdx.x * blockDim.x; t0 < pl.end;
+       t0 += (unsigned long long)gridDim.x * blockDim.x) {
+    const unsigned long long i = t0 + tid;
+    const bool valid = i < pl.end;
+    const unsigned short* rec = S + i * R;
+    unsigned int v1 = 0xFFFFu, v2 = 0xFFFFu, vt = 0, vp = 0, rb = 0, deg = 0;
+    unsigned long long sig = 0;
+    if (valid) {
+      v1 = ldcg16(rec);
+      v2 = ldcg16(rec + 1);
+      vt = ldcg16(rec + t - 1);
+      vp = ldcg16(rec + t - 2);
+      for (unsigned int k = 1; k + 1 < t; ++k) sig |= 1ull << (ldcg16(rec + k) & 63u);
+      rb = nrow[vt];
+      deg = nrow[vt + 1] - rb;
+    }
+    for (unsigned int w0 = 0; __syncthreads_or(valid && w0 < deg); w0 += 32) {
+      unsigned int mask = 0;
+      if (valid && w0 < deg) {
+        const unsigned int qend = min(deg, w0 + 32);
+        for (unsigned int q = w0; q < qend; ++q) {
+          const unsigned int v = ncol[rb + q];
+          if (v <= v2 || v == vp) continue;
+          bool close = false, chord = false;
+          const unsigned int e1 = nrow[v + 1];
+          for (unsigned int e = nrow[v]; e < e1 && !chord; ++e) {
+            const unsigned int w = ncol[e];
+            if (w < v2 || w == vt) continue;
+            if (w == v1) {
+              close = true;
+              continue;
+            }
+            if ((sig >> (w & 63u)) & 1ull)
+              for (unsigned int k = 1; k + 1 < t; ++k)
+                if (ldcg16(rec + k) == w) {
+                  chord = true;
+                  break;
+                }
+          }
+          if (chord) continue;
+          if (close) {
+            if (close_ok) {
+              ++ncyc;
+              unsigned long long hs = rtab[v];
+              for (unsigned int k = 0; k < t; ++k) hs += rtab[ldcg16(rec + k)];
+              hacc += mix64(hs + (unsigned long long)(t + 1) * kGamma);
+              if (p.cyc_vert)
+                emit_cycle(p, t + 1, [&](unsigned int j) -> unsigned int {
+                  return j < t ? (unsigned int)ldcg16(rec + j) : v;
+                });
+            }
+          } else if (store) {
+            mask |= 1u << (q - w0);
+          }
+        }
+      }
+      if (store) {
+        const unsigned long long off = tile_slots(__popc(mask), &p.ctl->cnt[s % 3], s_warp, s_base);
+        if (mask) {
+          unsigned long long slot = off;
+          while (mask) {
+            const unsigned int q = __ffs(mask) - 1;
+            mask &= mask - 1;
+            const unsigned int v = ncol[rb + w0 + q];
+            if (slot < ds) {
+              unsigned short* out = D + slot * R2;
+              for (unsigned int k = 0; k < t; ++k) out[k] = ldcg16(rec + k);
+              out[t] = (unsigned short)v;
+              for (unsigned int k = t + 1; k < R2; ++k) out[k] = 0xFFFFu;
+              if (bound_ok) nbound += nrow[v + 1] - nrow[v] - 1;
+            } else {
+              set_err(p.ctl, kDevBounds, 2);
+            }
+            ++slot;
+          }
+        }
+      }
+    }
+  }
+  block_sum3_u64(ncyc, hacc, nbound, s_red);
   if (threadIdx.x == 0) {
     if (ncyc) atomicAdd(&p.hist[t + 1], ncyc);
     if (hacc) atomicAdd(p.hash, hacc);
@@ -816,8 +780,7 @@ __global__ void __launch_bounds__(kMaxThreads, KindTraits<K>::minB) engine_kerne
       constexpr int CAP = KindTraits<K>::cap;
       if (pl.t <= 16) process_csr_coop<16>(p, pl, nrow, ncol, rtab);
       else if (CAP >= 32 && pl.t <= 32) process_csr_coop<(CAP >= 32 ? 32 : 16)>(p, pl, nrow, ncol, rtab);
-      else if (CAP >= 64 && pl.t <= 64) process_csr<(CAP >= 64 ? 64 : 16)>(p, pl, nrow, ncol, rtab, s_warp, s_red, &s_base);
-      else process_csr<0>(p, pl, nrow, ncol, rtab, s_warp, s_red, &s_base);
+      else process_csr_long(p, pl, nrow, ncol, rtab, s_warp, s_red, &s_base);
     } else {
       process_bitset<K>(p, pl, adj, rtab, s_warp, s_red, &s_base);
     }

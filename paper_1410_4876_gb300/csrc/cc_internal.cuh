@@ -17,7 +17,8 @@
 //       H  sum of r(original id) over the path's vertices (running cycle-hash input).
 //       M  v_1 | v_t << 16 (relabelled ids).
 //   bitset, many graphs (n <= 64, W = 1): same planes, M = v1 | vt<<6 | t<<12 | slot<<18.
-//   CSR, one graph: t planes of u16 relabelled ids P_0..P_{t-1} (the path in order).
+//   CSR, one graph: one record per path, its relabelled u16 ids in order padded with 0xFFFF
+//       to a multiple of 8 ids (16-byte vector accesses).
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -409,12 +410,13 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned 
 __host__ __device__ __forceinline__ unsigned long long round_up(unsigned long long x, unsigned long long a) {
   return (x + a - 1) / a * a;
 }
-// Record bytes: bitset planes (8W + 12), CSR planes (2t).
+// Record bytes: bitset planes (8W + 12), CSR records (2 csr_rec_u16(t)).
 __host__ __device__ __forceinline__ unsigned long long bitset_region_bytes(unsigned long long stride, int W) {
   return round_up(stride * (8ull * W + 12ull), 256);
 }
+__host__ __device__ __forceinline__ unsigned int csr_rec_u16(unsigned int t) { return (t + 7u) & ~7u; }
 __host__ __device__ __forceinline__ unsigned long long csr_region_bytes(unsigned long long stride, unsigned t) {
-  return round_up(stride * 2ull * t, 256);
+  return round_up(stride * 2ull * csr_rec_u16(t), 256);
 }
 
 // Kernel launchers (defined in the .cu files).

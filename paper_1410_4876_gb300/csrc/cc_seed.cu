@@ -335,7 +335,7 @@ __device__ __forceinline__ bool csr_adjacent(const unsigned int* nrow, const uns
   return false;
 }
 
-// One thread per directed CSR entry (u, x) with x > u.  Frame 0: planes P0, P1, P2 (u16).
+// One thread per directed CSR entry (u, x) with x > u.  Frame 0: one record per triplet.
 __global__ void __launch_bounds__(256) seed_csr_kernel(EngineParams p, unsigned long long stride) {
   const unsigned int n = p.n, L = p.L;
   const unsigned int m2 = p.nrow[n];
@@ -383,15 +383,13 @@ __global__ void __launch_bounds__(256) seed_csr_kernel(EngineParams p, unsigned 
   base = __shfl_sync(0xffffffffu, base, 31) + (incl - npath);
   unsigned long long nb = 0;
   if (npath) {
-    unsigned short* P0 = (unsigned short*)p.arena;
+    uint4* R0 = reinterpret_cast<uint4*>(p.arena);  // one 8-id record per triplet
     unsigned long long slot = base;
     for (unsigned int f = e + 1; f < rend; ++f) {
       const unsigned int y = p.ncol[f];
       if (csr_adjacent(p.nrow, p.ncol, x, y)) continue;
       if (slot >= stride) { set_err(p.ctl, kDevSeedCap, 0); break; }
-      P0[slot] = (unsigned short)x;
-      P0[stride + slot] = (unsigned short)u;
-      P0[2 * stride + slot] = (unsigned short)y;
+      R0[slot] = make_uint4(x | (u << 16), y | 0xFFFF0000u, 0xFFFFFFFFu, 0xFFFFFFFFu);
       if (L > 4) nb += p.nrow[y + 1] - p.nrow[y] - 1;  // bound on this path's children
       ++slot;
     }
