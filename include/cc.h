@@ -84,7 +84,12 @@ typedef struct cc_options {
   uint32_t blocks_per_sm;      /* persistent blocks per SM; 0 = occupancy limit, at most 4 */
   uint32_t mode;               /* CC_MODE_*                                               */
   uint32_t spin_limit;         /* grid-barrier wait limit in polls; 0 = default (~8 s)    */
+  uint32_t flags;              /* CC_FLAG_*                                               */
 } cc_options;
+
+/* cc_options.flags */
+#define CC_FLAG_NO_CLUSTER_PHASE 1u /* bitset graphs: skip the thread-block-cluster phase that  */
+                                    /* expands small levels before the persistent grid starts  */
 
 /* Build limits. */
 typedef struct cc_limits {
@@ -107,6 +112,8 @@ typedef struct cc_run_info {
   uint32_t spilled;        /* 1 if some level was expanded in depth-first chunks      */
   uint32_t pad;
   uint64_t peak_bytes;     /* largest arena extent in use                             */
+  int32_t dev_error;       /* device-side error word (0 = none; diagnostics)          */
+  int32_t dev_error_info;  /* where it was raised                                     */
 } cc_run_info;
 
 /* Optional cycle list.  Set the capacities and pointers; the call fills count,

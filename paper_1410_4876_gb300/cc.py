@@ -50,7 +50,11 @@ class cc_options(ctypes.Structure):
         ("blocks_per_sm", ctypes.c_uint32),
         ("mode", ctypes.c_uint32),
         ("spin_limit", ctypes.c_uint32),
+        ("flags", ctypes.c_uint32),
     ]
+
+
+CC_FLAG_NO_CLUSTER_PHASE = 1
 
 
 class cc_limits(ctypes.Structure):
@@ -75,6 +79,8 @@ class cc_run_info(ctypes.Structure):
         ("spilled", ctypes.c_uint32),
         ("pad", ctypes.c_uint32),
         ("peak_bytes", ctypes.c_uint64),
+        ("dev_error", ctypes.c_int32),
+        ("dev_error_info", ctypes.c_int32),
     ]
 
 
@@ -257,7 +263,8 @@ class Context:
     caching allocator and the work runs on torch's current stream."""
 
     def __init__(self, frontier_bytes: int = 0, mode: int = CC_MODE_AUTO, threads_per_block: int = 0,
-                 blocks_per_sm: int = 0, spin_limit: int = 0, use_torch: bool = False, stream: int = 0):
+                 blocks_per_sm: int = 0, spin_limit: int = 0, use_torch: bool = False, stream: int = 0,
+                 flags: int = 0):
         self._ws = None
         opts = cc_options()
         opts.frontier_bytes = frontier_bytes
@@ -266,6 +273,7 @@ class Context:
         opts.blocks_per_sm = blocks_per_sm
         opts.spin_limit = spin_limit
         opts.stream = stream or None
+        opts.flags = flags
         if use_torch:
             import torch
             nbytes = frontier_bytes or (1 << 30)

@@ -321,6 +321,22 @@ extern "C" cc_status cc_enumerate(cc_graph* g, uint32_t max_len, uint64_t* out_h
   ok(launch_label_single(g->d_row, g->d_col, n, (unsigned int)(2 * g->m), W, g->d_perm, g->d_adj, g->d_rtab, g->d_nrow, g->d_ncol, st));
   ok(launch_seed_single(kind, p, seed_stride, st));
   ok(cudaEventRecord(c->ev3, st));
+  if (!is_csr(kind) && !(c->opts.flags & CC_FLAG_NO_CLUSTER_PHASE)) {
+    // small levels first on one thread-block cluster (hardware barrier between levels),
+    // then the persistent grid resumes from the state it leaves
+    const unsigned long long key = (unsigned long long)kind | ((unsigned long long)smem << 8);
+    int cs = -1;
+    for (auto& kv : c->cluster_sizes)
+      if (kv.first == key) cs = kv.second;
+    if (cs < 0) {
+      cs = small_cluster_size(kind, smem);
+      c->cluster_sizes.push_back({key, cs});
+    }
+    if (cs > 0) {
+      ok(launch_small_engine(kind, p, cs, smem, 2ull * cs * 1024, st));
+      p.fresh = 0;
+    }
+  }
   ok(launch_engine(kind, p, grid, block, smem, st));
   ok(cudaEventRecord(c->ev1, st));
   ok(cudaMemcpyAsync(c->h_res, c->d_res, words * 8, cudaMemcpyDeviceToHost, st));
@@ -330,6 +346,9 @@ extern "C" cc_status cc_enumerate(cc_graph* g, uint32_t max_len, uint64_t* out_h
   if (e != cudaSuccess) {
     (void)cudaGetLastError();
     free_cyc();
+    info.dev_error = -(int)e;  // a CUDA API error: its code, negated
+    c->last = info;
+    if (out_info) *out_info = info;
     return cuda_status(e);
   }
   float ms1 = 0, ms2 = 0, ms3 = 0;
@@ -347,6 +366,8 @@ extern "C" cc_status cc_enumerate(cc_graph* g, uint32_t max_len, uint64_t* out_h
   c->last_t_start = h.t_start;
   info.steps = h.step;
   info.spilled = h.spilled;
+  info.dev_error = h.err;
+  info.dev_error_info = h.err_info;
   info.peak_bytes = h.peak;
   for (unsigned int k = 0; k <= L; ++k) {
     info.cycles += c->h_res[k];

@@ -16,7 +16,8 @@
 
 namespace cc {
 
-constexpr int kMaxThreads = 256;
+constexpr int kMaxThreads = 256;    // persistent grid blocks
+constexpr int kSmallThreads = 1024; // small-phase cluster blocks
 
 struct StepPlan {
   unsigned long long src_base, src_stride, begin, end;
@@ -689,12 +690,23 @@ __device__ __forceinline__ void process_csr_long(const EngineParams& p, const St
 
 // ------------------------------------------------------------------ the persistent kernel
 
-template <Kind K>
-__global__ void __launch_bounds__(kMaxThreads, KindTraits<K>::minB) engine_kernel(EngineParams p) {
+// Hardware barrier of a thread-block cluster (all threads of all CTAs of the cluster),
+// with release/acquire ordering of global and shared memory at cluster scope.
+__device__ __forceinline__ void cluster_barrier() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+// NT threads per block.  NT = 256: the persistent grid (cooperative launch, grid barrier).
+// NT = 1024: the small phase, one thread-block cluster whose steps are separated by the
+// hardware cluster barrier; it runs while the frames are small (p.handover) and leaves
+// the state for the grid launch that follows.  Every CTA computes the same plan, so all
+// CTAs of the cluster execute the same sequence of cluster barriers.
+template <Kind K, int NT>
+__global__ void __launch_bounds__(NT, NT >= 1024 ? 1 : KindTraits<K>::minB) engine_kernel(EngineParams p) {
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ StepPlan pl;
   __shared__ LocalState st;
-  __shared__ unsigned int s_warp[kMaxThreads / 32 + 1];
+  __shared__ unsigned int s_warp[NT / 32 + 1];
   __shared__ unsigned long long s_red[96];
   __shared__ unsigned long long s_base;
   __shared__ __align__(8) unsigned long long s_mbar;
@@ -771,6 +783,9 @@ __global__ void __launch_bounds__(kMaxThreads, KindTraits<K>::minB) engine_kerne
     if (tid == 0) {
       bool go = p.max_steps == 0 || steps_here < p.max_steps;
       if (go) go = plan_step<K>(p, st, pl);
+      // small phase: stop before a level that is too large for one cluster (the plan has
+      // only popped finished frames, which the state written back below keeps)
+      if (go && p.handover && pl.end - pl.begin > p.handover) go = false;
       pl.done = go ? 0u : 1u;
       pl.s = s;
     }
@@ -788,7 +803,11 @@ __global__ void __launch_bounds__(kMaxThreads, KindTraits<K>::minB) engine_kerne
       p.ctl->cnt[(s + 1) % 3] = 0;
       p.ctl->nxt[(s + 1) % 3] = 0;
     }
-    if (!grid_barrier(p.ctl, gridDim.x, p.spin_limit, st.gen)) break;
+    if (p.cluster) {
+      cluster_barrier();
+    } else if (!grid_barrier(p.ctl, gridDim.x, p.spin_limit, st.gen)) {
+      break;
+    }
     if (tid == 0) {
       const unsigned long long c = ld_relaxed_u64(&p.ctl->cnt[s % 3]);
       const unsigned long long nx = ld_relaxed_u64(&p.ctl->nxt[s % 3]);
@@ -816,15 +835,24 @@ __global__ void __launch_bounds__(kMaxThreads, KindTraits<K>::minB) engine_kerne
 
 static const void* engine_fn(Kind k) {
   switch (k) {
-    case Kind::Bitset1: return (const void*)engine_kernel<Kind::Bitset1>;
-    case Kind::Bitset2: return (const void*)engine_kernel<Kind::Bitset2>;
-    case Kind::Bitset4: return (const void*)engine_kernel<Kind::Bitset4>;
-    case Kind::Multi: return (const void*)engine_kernel<Kind::Multi>;
-    case Kind::Csr: return (const void*)engine_kernel<Kind::Csr>;
-    case Kind::Csr16: return (const void*)engine_kernel<Kind::Csr16>;
-    case Kind::Csr32: return (const void*)engine_kernel<Kind::Csr32>;
+    case Kind::Bitset1: return (const void*)engine_kernel<Kind::Bitset1, kMaxThreads>;
+    case Kind::Bitset2: return (const void*)engine_kernel<Kind::Bitset2, kMaxThreads>;
+    case Kind::Bitset4: return (const void*)engine_kernel<Kind::Bitset4, kMaxThreads>;
+    case Kind::Multi: return (const void*)engine_kernel<Kind::Multi, kMaxThreads>;
+    case Kind::Csr: return (const void*)engine_kernel<Kind::Csr, kMaxThreads>;
+    case Kind::Csr16: return (const void*)engine_kernel<Kind::Csr16, kMaxThreads>;
+    case Kind::Csr32: return (const void*)engine_kernel<Kind::Csr32, kMaxThreads>;
   }
   return nullptr;
+}
+
+static const void* small_engine_fn(Kind k) {
+  switch (k) {
+    case Kind::Bitset1: return (const void*)engine_kernel<Kind::Bitset1, kSmallThreads>;
+    case Kind::Bitset2: return (const void*)engine_kernel<Kind::Bitset2, kSmallThreads>;
+    case Kind::Bitset4: return (const void*)engine_kernel<Kind::Bitset4, kSmallThreads>;
+    default: return nullptr;
+  }
 }
 
 cudaError_t engine_occupancy(Kind kind, int block, size_t smem, int* blocks_per_sm) {
@@ -839,8 +867,65 @@ cudaError_t launch_engine(Kind kind, const EngineParams& p, int grid, int block,
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   EngineParams copy = p;
+  copy.cluster = 0;
+  copy.handover = 0;
   void* args[] = {(void*)&copy};
   return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(block), args, smem, st);
+}
+
+// Largest usable cluster (at most 16 CTAs of kSmallThreads threads), 0 if clusters of this
+// kernel cannot be launched (then the small phase is skipped).
+int small_cluster_size(Kind kind, size_t smem) {
+  const void* fn = small_engine_fn(kind);
+  if (!fn) return 0;
+  if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+      cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return 0;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(16);
+  cfg.blockDim = dim3(kSmallThreads);
+  cfg.dynamicSmemBytes = smem;
+  cudaLaunchAttribute attr;
+  attr.id = cudaLaunchAttributeClusterDimension;
+  attr.val.clusterDim.x = 16;
+  attr.val.clusterDim.y = 1;
+  attr.val.clusterDim.z = 1;
+  cfg.attrs = &attr;
+  cfg.numAttrs = 1;
+  int cs = 0;
+  if (cudaOccupancyMaxPotentialClusterSize(&cs, fn, &cfg) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return 0;
+  }
+  return cs >= 16 ? 16 : (cs >= 8 ? 8 : 0);
+}
+
+cudaError_t launch_small_engine(Kind kind, const EngineParams& p, int cluster, size_t smem,
+                                unsigned long long handover, cudaStream_t st) {
+  const void* fn = small_engine_fn(kind);
+  if (!fn || cluster <= 0) return cudaErrorInvalidValue;
+  // the attribute is per kernel, and the previous launch may have needed less
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  EngineParams copy = p;
+  copy.cluster = 1;
+  copy.handover = handover;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(cluster);
+  cfg.blockDim = dim3(kSmallThreads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr;
+  attr.id = cudaLaunchAttributeClusterDimension;
+  attr.val.clusterDim.x = cluster;
+  attr.val.clusterDim.y = 1;
+  attr.val.clusterDim.z = 1;
+  cfg.attrs = &attr;
+  cfg.numAttrs = 1;
+  void* args[] = {(void*)&copy};
+  return cudaLaunchKernelExC(&cfg, fn, args);
 }
 
 }  // namespace cc

@@ -44,6 +44,7 @@ struct cc_context {
   unsigned long long* d_trace = nullptr;  // per-step end time | paths expanded (last call)
   unsigned int trace_cap = 0;
   cc_run_info last{};
+  std::vector<std::pair<unsigned long long, int>> cluster_sizes;  // (kind | smem << 8) -> size
   unsigned long long last_t_start = 0;  // globaltimer at the start of the last expansion
   // batch state
   struct Batch {

@@ -138,6 +138,9 @@ struct EngineParams {
   unsigned int row_bytes;          // CSR staging: bytes of the row offsets (16-byte padded)
   unsigned long long seed_stride;  // frame 0 records per plane
   unsigned long long seed_bytes;   // frame 0 region bytes
+  unsigned int cluster;            // 1: one thread-block cluster, hardware cluster barrier
+  unsigned int pad_;
+  unsigned long long handover;     // cluster phase: stop before expanding more paths than this
 };
 
 #ifdef __CUDACC__
@@ -429,6 +432,9 @@ cudaError_t launch_seed_single(Kind kind, const EngineParams& p, unsigned long l
 cudaError_t launch_engine(Kind kind, const EngineParams& p, int grid, int block, size_t smem,
                           cudaStream_t st);
 cudaError_t engine_occupancy(Kind kind, int block, size_t smem, int* blocks_per_sm);
+int small_cluster_size(Kind kind, size_t smem);
+cudaError_t launch_small_engine(Kind kind, const EngineParams& p, int cluster, size_t smem,
+                                unsigned long long handover, cudaStream_t st);
 size_t engine_smem_bytes(Kind kind, const EngineParams& p, int block);
 cudaError_t launch_label_seed_multi(const unsigned int* row_ptr_all, const unsigned long long* row_off,
                                     const unsigned int* col_all, const unsigned long long* col_off,

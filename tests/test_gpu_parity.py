@@ -170,7 +170,8 @@ def test_capacity_error(cc):
 def test_barrier_timeout_reports_status(cc):
     # a poll limit of one makes the grid barrier give up at once: the call must return
     # CC_ERR_TIMEOUT (no fault, no hang) and a later call on a fresh context must work
-    with cc.Context(spin_limit=1) as c:
+    # (the cluster phase, which has no polled wait, is switched off so the grid runs)
+    with cc.Context(spin_limit=1, flags=cc.CC_FLAG_NO_CLUSTER_PHASE) as c:
         with pytest.raises(cc.CCError) as e:
             c.enumerate(I.grid(6, 6))
         assert e.value.status == cc.CC_ERR_TIMEOUT
@@ -279,3 +280,30 @@ def test_batch_spill(cc):
         hist, hsh, paths, done, info = c.batch(graphs, max_len=8)
     assert info.spilled == 1
     _check_batch(graphs, _oracle_many(graphs, 8), hist, hsh, paths)
+
+
+def test_cluster_phase_equals_grid_only(cc):
+    # small levels run on one thread-block cluster before the persistent grid takes over;
+    # switching that phase off must not change any result
+    graphs = [I.grid(6, 6), I.grid(8, 8), I.gnp(60, 0.15, 7), I.wheel(100), I.gnp(100, 2.4 / 100, 100),
+              I.complete_bipartite(8, 8)] + _small_graphs(40, 606)
+    with cc.Context(frontier_bytes=2 << 30) as a, \
+            cc.Context(frontier_bytes=2 << 30, flags=cc.CC_FLAG_NO_CLUSTER_PHASE) as b:
+        for g in graphs:
+            ra, rb = a.enumerate(g), b.enumerate(g)
+            assert ra.hist.tolist() == rb.hist.tolist() and ra.hash == rb.hash
+            assert ra.tcount.tolist() == rb.tcount.tolist()
+            assert ra.info.steps == rb.info.steps
+        for g in graphs[6:]:
+            _same(a.enumerate(g), oracle.enumerate_cycles(g))
+
+
+def test_trace_matches_level_counts(cc, ctx):
+    g = I.grid(7, 7)
+    r = ctx.enumerate(g)
+    t_ns, expanded = cc.cc_get_trace(ctx.handle)
+    assert len(expanded) == r.info.steps
+    # without spilling every step expands one whole level: the trace lists |T_3|..|T_{L'-1}|
+    nz = [int(x) for x in r.tcount if x]
+    assert [int(x) for x in expanded] == nz
+    assert (np.diff(t_ns.astype(np.int64)) >= 0).all()
