@@ -171,14 +171,14 @@ def run_reference(args, work, desc):
     if rank != 0:
         return
     cores = os.cpu_count() or 1
-    nparts = cores * 2
-    # each step: a quarter of the triplet parts (rotating), on all host cores
+    nparts = cores * 4
+    # each step: a quarter of the triplet parts (rotating), one part per host core
     for w in range(args.warmup):
-        cpu_baseline(work, sample_parts=list(range(w % 4, nparts, 4)))
+        cpu_baseline(work, parts_per_core=4, sample_parts=list(range(w % 4, nparts, 4)))
     tot_c = tot_p = 0
     tot_t = 0.0
     for s in range(args.steps):
-        c, p, dt, _, _, _ = cpu_baseline(work, sample_parts=list(range(s % 4, nparts, 4)))
+        c, p, dt, _, _, _ = cpu_baseline(work, parts_per_core=4, sample_parts=list(range(s % 4, nparts, 4)))
         tot_c += c
         tot_p += p
         tot_t += dt

@@ -249,7 +249,9 @@ __device__ __forceinline__ void process_bitset(const EngineParams& p, const Step
   // thread-interleaved grid stride: path i0 + j*T (j < P) for thread gtid, T threads in
   // the grid, so the last round of a step is spread over every thread (no block tiles)
   const unsigned long long T = (unsigned long long)gridDim.x * blockDim.x;
-  const unsigned long long gwarp = ((unsigned long long)blockIdx.x * blockDim.x + tid) & ~31ull;
+  // warp w of block b takes the (w * gridDim + b)-th group of 32 paths, so the warps of a
+  // small step land on different SMs
+  const unsigned long long gwarp = ((unsigned long long)(tid >> 5) * gridDim.x + blockIdx.x) * 32ull;
   // the bound is tested on the warp's first thread so every lane runs the same iterations
   // (the body uses full-warp collectives)
   for (unsigned long long wb = pl.begin + gwarp; wb < pl.end; wb += P * T) {
@@ -457,7 +459,7 @@ __device__ __forceinline__ void process_csr_coop(const EngineParams& p, const St
   const unsigned long long s = pl.s;
   unsigned long long ncyc = 0, hacc = 0, nbound = 0;
   const unsigned long long nwarps = (unsigned long long)gridDim.x * (blockDim.x >> 5);
-  for (unsigned long long w0 = pl.begin + ((unsigned long long)blockIdx.x * (blockDim.x >> 5) + wid) * 32;
+  for (unsigned long long w0 = pl.begin + ((unsigned long long)wid * gridDim.x + blockIdx.x) * 32;
        w0 < pl.end; w0 += nwarps * 32) {
     const unsigned long long i = w0 + lane;
     const bool valid = i < pl.end;
