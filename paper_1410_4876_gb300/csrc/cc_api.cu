@@ -132,6 +132,7 @@ extern "C" cc_status cc_graph_load(cc_context* c, uint32_t n, const uint32_t* ro
   g->ncol_bytes = r16(2ull * row_ptr[n]);
   g->rtab_bytes = r16(8ull * npad);
   g->adj_bytes = g->W ? r16(8ull * npad * g->W) : 0;
+  g->nsig_bytes = r16(16ull * std::max<uint32_t>(n, 1));
   auto fail = [&](cc_status st) {
     cc_graph_free(g);
     return st;
@@ -142,6 +143,7 @@ extern "C" cc_status cc_graph_load(cc_context* c, uint32_t n, const uint32_t* ro
   if ((s = dev_alloc(c, (void**)&g->d_rtab, g->rtab_bytes))) return fail(s);
   if ((s = dev_alloc(c, (void**)&g->d_nrow, g->nrow_bytes))) return fail(s);
   if ((s = dev_alloc(c, (void**)&g->d_ncol, g->ncol_bytes))) return fail(s);
+  if ((s = dev_alloc(c, (void**)&g->d_nsig, g->nsig_bytes))) return fail(s);
   if (g->W && (s = dev_alloc(c, (void**)&g->d_adj, g->adj_bytes))) return fail(s);
   if (cudaMemcpyAsync(g->d_row, row_ptr, 4ull * (n + 1), cudaMemcpyHostToDevice, c->stream) != cudaSuccess ||
       (row_ptr[n] && cudaMemcpyAsync(g->d_col, sorted.data(), 4ull * row_ptr[n], cudaMemcpyHostToDevice,
@@ -149,6 +151,7 @@ extern "C" cc_status cc_graph_load(cc_context* c, uint32_t n, const uint32_t* ro
       cudaMemsetAsync(g->d_nrow, 0, g->nrow_bytes, c->stream) != cudaSuccess ||
       cudaMemsetAsync(g->d_ncol, 0, g->ncol_bytes, c->stream) != cudaSuccess ||
       cudaMemsetAsync(g->d_rtab, 0, g->rtab_bytes, c->stream) != cudaSuccess ||
+      cudaMemsetAsync(g->d_nsig, 0, g->nsig_bytes, c->stream) != cudaSuccess ||
       cudaStreamSynchronize(c->stream) != cudaSuccess) {
     (void)cudaGetLastError();
     return fail(CC_ERR_CUDA);
@@ -167,6 +170,7 @@ extern "C" void cc_graph_free(cc_graph* g) {
   dev_free(c, g->d_rtab);
   dev_free(c, g->d_nrow);
   dev_free(c, g->d_ncol);
+  dev_free(c, g->d_nsig);
   delete g;
 }
 
@@ -251,6 +255,7 @@ extern "C" cc_status cc_enumerate(cc_graph* g, uint32_t max_len, uint64_t* out_h
   p.rtab = g->d_rtab;
   p.nrow = g->d_nrow;
   p.ncol = g->d_ncol;
+  p.nsig = g->d_nsig;
   p.perm = g->d_perm;
   p.hist = d_hist;
   p.hash = d_hash;
@@ -287,12 +292,14 @@ extern "C" cc_status cc_enumerate(cc_graph* g, uint32_t max_len, uint64_t* out_h
   // graph staging into shared memory
   size_t smem = 0;
   if (is_csr(kind)) {
-    const size_t need = g->nrow_bytes + g->ncol_bytes + g->rtab_bytes;
+    // rows, neighbours and neighbour signatures (the r-table is read only when a cycle
+    // closes and stays in global memory)
+    const size_t need = g->nrow_bytes + g->ncol_bytes + g->nsig_bytes;
     if (need <= 160 * 1024) {
       p.smem_graph = 1;
       p.row_bytes = (unsigned int)g->nrow_bytes;
       p.adj_bytes = (unsigned int)(g->nrow_bytes + g->ncol_bytes);
-      p.rtab_bytes = (unsigned int)g->rtab_bytes;
+      p.nsig_bytes = (unsigned int)g->nsig_bytes;
       smem = need;
     }
   } else {
@@ -318,7 +325,7 @@ extern "C" cc_status cc_enumerate(cc_graph* g, uint32_t max_len, uint64_t* out_h
   ok(cudaEventRecord(c->ev0, st));
   ok(cudaMemsetAsync(c->ctl, 0, sizeof(Control), st));
   ok(cudaMemsetAsync(c->d_res, 0, words * 8, st));
-  ok(launch_label_single(g->d_row, g->d_col, n, (unsigned int)(2 * g->m), W, g->d_perm, g->d_adj, g->d_rtab, g->d_nrow, g->d_ncol, st));
+  ok(launch_label_single(g->d_row, g->d_col, n, (unsigned int)(2 * g->m), W, g->d_perm, g->d_adj, g->d_rtab, g->d_nrow, g->d_ncol, g->d_nsig, st));
   ok(launch_seed_single(kind, p, seed_stride, st));
   ok(cudaEventRecord(c->ev3, st));
   if (!is_csr(kind) && !(c->opts.flags & CC_FLAG_NO_CLUSTER_PHASE)) {

@@ -80,7 +80,8 @@ struct cc_graph {
   unsigned long long* d_rtab = nullptr;
   unsigned int* d_nrow = nullptr;   // relabelled CSR
   unsigned short* d_ncol = nullptr;
-  size_t nrow_bytes = 0, ncol_bytes = 0, adj_bytes = 0, rtab_bytes = 0;
+  unsigned long long* d_nsig = nullptr;  // neighbour signatures of the relabelled CSR [2n]
+  size_t nrow_bytes = 0, ncol_bytes = 0, adj_bytes = 0, rtab_bytes = 0, nsig_bytes = 0;
 };
 
 // ------------------------------------------------------------------ helpers

@@ -38,6 +38,13 @@ __host__ __device__ __forceinline__ unsigned long long vertex_r(unsigned int v) 
   return mix64((unsigned long long)(v + 1ull) * kGamma);
 }
 
+// Neighbour signatures of the CSR expansion: vertex x (relabelled id) stands for bit
+// sig_bit(x) of a 128-bit word pair (Knuth's multiplicative hash, top 7 bits).  nsig(v) is
+// the OR over Adj(v); a path's interior signature is the OR over v2..v_{t-1}.  Disjoint
+// signatures prove that no neighbour of v lies on the interior (no chord); a set bit only
+// means "maybe", and the exact test decides.
+__host__ __device__ __forceinline__ unsigned int sig_bit(unsigned int x) { return (x * 2654435761u) >> 25; }
+
 // Device error words (Control::err).
 enum : int {
   kDevOk = 0,
@@ -139,7 +146,8 @@ struct EngineParams {
   unsigned long long seed_stride;  // frame 0 records per plane
   unsigned long long seed_bytes;   // frame 0 region bytes
   unsigned int cluster;            // 1: one thread-block cluster, hardware cluster barrier
-  unsigned int pad_;
+  unsigned int nsig_bytes;         // CSR staging: bytes of the neighbour signatures
+  const unsigned long long* nsig;  // CSR: neighbour signature of each vertex, 2 words [n]
   unsigned long long handover;     // cluster phase: stop before expanding more paths than this
 };
 
@@ -397,6 +405,11 @@ __device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, unsign
       "l"(src), "r"(bytes), "r"(smem_addr(bar))
       : "memory");
 }
+// L2 prefetch of a contiguous global range by the bulk-copy engine (no registers, no
+// shared memory); address and size are multiples of 16 bytes.
+__device__ __forceinline__ void bulk_prefetch_l2(const void* src, unsigned int bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
+}
 __device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned int parity) {
   unsigned int ok;
   asm volatile(
@@ -426,7 +439,7 @@ __host__ __device__ __forceinline__ unsigned long long csr_region_bytes(unsigned
 cudaError_t launch_label_single(const unsigned int* row_ptr, const unsigned int* col, unsigned int n,
                                 unsigned int nnz, int W, unsigned int* perm, unsigned long long* adj,
                                 unsigned long long* rtab, unsigned int* nrow, unsigned short* ncol,
-                                cudaStream_t st);
+                                unsigned long long* nsig, cudaStream_t st);
 cudaError_t launch_seed_single(Kind kind, const EngineParams& p, unsigned long long seed_stride,
                                cudaStream_t st);
 cudaError_t launch_engine(Kind kind, const EngineParams& p, int grid, int block, size_t smem,

@@ -181,7 +181,7 @@ extern "C" cc_status cc_enumerate_noalloc(uint32_t n, const uint32_t* row_ptr, c
   ok(cudaMemcpyAsync(d_row, row_ptr, 4ull * (n + 1), cudaMemcpyHostToDevice, st));
   if (row_ptr[n]) ok(cudaMemcpyAsync(d_col, col_idx, 4ull * row_ptr[n], cudaMemcpyHostToDevice, st));
   ok(cudaMemsetAsync(d_rtab, 0, p.rtab_bytes, st));
-  ok(launch_label_single(d_row, d_col, n, row_ptr[n], W, d_perm, d_adj, d_rtab, d_nrow, d_ncol, st));
+  ok(launch_label_single(d_row, d_col, n, row_ptr[n], W, d_perm, d_adj, d_rtab, d_nrow, d_ncol, nullptr, st));
   ok(launch_seed_single(kind, p, p.seed_stride, st));
   ok(launch_engine(kind, p, grid, block, smem, st));
   Control h;

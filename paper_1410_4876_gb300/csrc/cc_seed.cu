@@ -22,7 +22,8 @@ __global__ void __launch_bounds__(1024) label_single_kernel(const unsigned int* 
                                                             const unsigned int* __restrict__ col, unsigned int n,
                                                             int W, unsigned int* perm, unsigned int* newid,
                                                             unsigned long long* adj, unsigned long long* rtab,
-                                                            unsigned int* nrow, unsigned short* ncol, int stage_csr) {
+                                                            unsigned int* nrow, unsigned short* ncol,
+                                                            unsigned long long* nsig, int stage_csr) {
   extern __shared__ unsigned int sm_label[];
   unsigned int* key = sm_label;
   const unsigned int G = (n + 31) / 32;
@@ -117,15 +118,25 @@ __global__ void __launch_bounds__(1024) label_single_kernel(const unsigned int* 
   }
   if (tid == 0) nrow[n] = total;
   __syncthreads();
-  // ... then each row sorted by rank (one warp per row; ids within a row are distinct)
+  // ... then each row sorted by rank (one warp per row; ids within a row are distinct),
+  // and the row's neighbour signature (OR of sig_bit over the row) next to it
   const unsigned int warp = tid >> 5, nwarps = blockDim.x >> 5;
   for (unsigned int r = warp; r < n; r += nwarps) {
     const unsigned int v = perm[r], b = row_ptr[v], d = row_ptr[v + 1] - b, out = nrow[r];
+    unsigned int sg[4] = {0, 0, 0, 0};
     for (unsigned int a = lane; a < d; a += 32) {
       const unsigned int x = newid[col[b + a]];
       unsigned int rank = 0;
       for (unsigned int c = 0; c < d; ++c) rank += newid[col[b + c]] < x;
       ncol[out + rank] = (unsigned short)x;
+      const unsigned int sb = sig_bit(x);
+      sg[sb >> 5] |= 1u << (sb & 31u);
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) sg[k] = __reduce_or_sync(0xffffffffu, sg[k]);
+    if (lane == 0) {
+      nsig[2ull * r] = (unsigned long long)sg[1] << 32 | sg[0];
+      nsig[2ull * r + 1] = (unsigned long long)sg[3] << 32 | sg[2];
     }
   }
 }
@@ -195,7 +206,8 @@ __global__ void __launch_bounds__(32) label_small_kernel(const unsigned int* __r
 
 cudaError_t launch_label_single(const unsigned int* row_ptr, const unsigned int* col, unsigned int n,
                                 unsigned int nnz, int W, unsigned int* perm, unsigned long long* adj,
-                                unsigned long long* rtab, unsigned int* nrow, unsigned short* ncol, cudaStream_t st) {
+                                unsigned long long* rtab, unsigned int* nrow, unsigned short* ncol,
+                                unsigned long long* nsig, cudaStream_t st) {
   if (W == 1 && n <= 64) {
     label_small_kernel<<<1, 32, 0, st>>>(row_ptr, col, n, perm, perm + n, adj, rtab);
     return cudaGetLastError();
@@ -207,7 +219,7 @@ cudaError_t launch_label_single(const unsigned int* row_ptr, const unsigned int*
   if (stage) smem += 4 * csr_words;
   cudaError_t e = cudaFuncSetAttribute(label_single_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  label_single_kernel<<<1, 1024, smem, st>>>(row_ptr, col, n, W, perm, perm + n, adj, rtab, nrow, ncol, stage);
+  label_single_kernel<<<1, 1024, smem, st>>>(row_ptr, col, n, W, perm, perm + n, adj, rtab, nrow, ncol, nsig, stage);
   return cudaGetLastError();
 }
 
