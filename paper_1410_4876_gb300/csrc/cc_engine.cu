@@ -60,6 +60,9 @@ struct KindTraits {
   // register allocation must allow (4 blocks = 64 registers per thread, 3 = 85, 2 = 128)
   static constexpr int P = K == Kind::Bitset4 ? 1 : (K == Kind::Bitset1 ? 3 : 2);
   static constexpr int minB = (K == Kind::Csr || K == Kind::Csr32) ? 2 : ((K == Kind::Multi || K == Kind::Csr16) ? 3 : 4);
+  // paths per thread per round of the flattened single-graph form (one slot atomic per
+  // warp per round)
+  static constexpr int PF = K == Kind::Bitset1 ? 3 : (K == Kind::Bitset2 ? 2 : 1);
 };
 
 template <Kind K>
@@ -415,6 +418,167 @@ __device__ __forceinline__ void process_bitset(const EngineParams& p, const Step
     if (nx) atomicAdd(&p.ctl->nxt[s % 3], nx);
     if (!MULTI && ncyc) atomicAdd(&p.hist[t + 1], ncyc);
     if (!MULTI && hacc) atomicAdd(p.hash, hacc);
+  }
+}
+
+// Single-graph bitset expansion with flattened output.  The per-path part (load B, H, M;
+// cand = Adj(vt) & ~B, close = cand & Adj(v1), child = cand & ~Adj(v1)) is as above, but
+// each path's B | Adj(vt), H and v1 are staged in shared memory and its children and
+// closings are listed as (path, vertex) entries.  The entries are then worked off with
+// one entry per lane: a child list takes its slots with one atomic and lane i writes
+// slot base + i, so each plane is stored contiguously; a closing list adds
+// h(C) = mix(H + r(v) + (t+1) gamma).  This replaces the per-lane loops over a path's
+// children, whose cost was set by the lane with the most children.
+template <int W, int P, int NT>
+struct FlatSmem {
+  static constexpr unsigned int CL = 64 * P > 256 ? 256 : 64 * P;  // list entries per warp
+  unsigned long long nb[NT / 32][P * 32 * W];  // B | Adj(vt) per staged path
+  unsigned long long h[NT / 32][P * 32];       // H per staged path
+  unsigned int v1[NT / 32][P * 32];            // v1 per staged path
+  unsigned int list[NT / 32][CL];              // entries: path << 8 | v
+};
+
+template <Kind K, int NT>
+__device__ __forceinline__ void process_bitset_flat(const EngineParams& p, const StepPlan& pl,
+                                                    const unsigned long long* adj, const unsigned long long* rtab,
+                                                    unsigned long long* s_red) {
+  constexpr int W = KindTraits<K>::W;
+  constexpr int P = KindTraits<K>::PF;
+  constexpr unsigned int CL = FlatSmem<W, P, NT>::CL;
+  __shared__ FlatSmem<W, P, NT> fs;
+  const unsigned int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  unsigned long long* snb = fs.nb[wid];
+  unsigned long long* sh = fs.h[wid];
+  unsigned int* sv1 = fs.v1[wid];
+  unsigned int* sl = fs.list[wid];
+  const unsigned long long ss = pl.src_stride, ds = pl.dst_stride;
+  const unsigned long long* sB = reinterpret_cast<const unsigned long long*>(p.arena + pl.src_base);
+  const unsigned long long* sH = sB + W * ss;
+  const unsigned int* sM = reinterpret_cast<const unsigned int*>(sH + ss);
+  unsigned long long* dB = reinterpret_cast<unsigned long long*>(p.arena + pl.dst_base);
+  unsigned long long* dH = dB + W * ds;
+  unsigned int* dM = reinterpret_cast<unsigned int*>(dH + ds);
+  const bool store = ds != 0;
+  const unsigned int t = pl.t, L = p.L;
+  const unsigned long long s = pl.s;
+  const bool close_ok = t + 1 <= L, next_ok = t + 2 < L;
+  const unsigned long long gam = (unsigned long long)(t + 1) * kGamma;
+  unsigned long long nx = 0, ncyc = 0, hacc = 0;
+  const unsigned long long T = (unsigned long long)gridDim.x * blockDim.x;
+  const unsigned long long gwarp = ((unsigned long long)wid * gridDim.x + blockIdx.x) * 32ull;
+
+  // children entries [0, n): slots from one atomic, lane i writes slot base + i
+  auto flush_children = [&](unsigned int n) {
+    __syncwarp();
+    unsigned long long base = 0;
+    if (lane == 0) base = atomicAdd(&p.ctl->cnt[s % 3], (unsigned long long)n);
+    base = __shfl_sync(0xffffffffu, base, 0);
+    for (unsigned int i = lane; i < n; i += 32) {
+      const unsigned int e = sl[i], pj = e >> 8, v = e & 0xFFu;
+      const unsigned long long slot = base + i;
+      if (slot < ds) {
+        const unsigned int v1 = sv1[pj];
+#pragma unroll
+        for (int q = 0; q < W; ++q) {
+          const unsigned long long nb = snb[pj * W + q];
+          dB[q * ds + slot] = nb;
+          if (next_ok) nx += __popcll(adj[(unsigned long long)v * W + q] & ~nb & ~adj[(unsigned long long)v1 * W + q]);
+        }
+        dH[slot] = sh[pj] + rtab[v];
+        dM[slot] = v1 | (v << 16);
+      } else {
+        set_err(p.ctl, kDevBounds, 1);
+      }
+    }
+    __syncwarp();
+  };
+  // closing entries [0, n)
+  auto flush_closings = [&](unsigned int n) {
+    __syncwarp();
+    for (unsigned int i = lane; i < n; i += 32) {
+      const unsigned int e = sl[i], pj = e >> 8, v = e & 0xFFu;
+      ++ncyc;
+      hacc += mix64(sh[pj] + rtab[v] + gam);
+    }
+    __syncwarp();
+  };
+  // list the set bits of m[j][k] (j < P, k < W) as entries, in chunks of CL, and work
+  // each chunk off with `work`
+  unsigned long long m[P][W];  // the masks being listed
+  auto list_and_work = [&](bool children) {
+    unsigned int cnt = 0;
+#pragma unroll
+    for (int j = 0; j < P; ++j)
+#pragma unroll
+      for (int k = 0; k < W; ++k) cnt += __popcll(m[j][k]);
+    unsigned int incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned int y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= (unsigned)o) incl += y;
+    }
+    const unsigned int excl = incl - cnt, total = __shfl_sync(0xffffffffu, incl, 31);
+    for (unsigned int c0 = 0; c0 < total; c0 += CL) {
+      if (cnt && excl < c0 + CL && excl + cnt > c0) {
+        unsigned int idx = excl;
+#pragma unroll
+        for (int j = 0; j < P; ++j)
+#pragma unroll
+          for (int k = 0; k < W; ++k) {
+            unsigned long long b = m[j][k];
+            while (b) {
+              const unsigned int v = 64u * k + __ffsll((long long)b) - 1;
+              b &= b - 1;
+              if (idx >= c0 && idx < c0 + CL) sl[idx - c0] = (unsigned int)(j * 32 + lane) << 8 | v;
+              ++idx;
+            }
+          }
+      }
+      if (children) flush_children(min(CL, total - c0));
+      else flush_closings(min(CL, total - c0));
+    }
+  };
+
+  for (unsigned long long wb = pl.begin + gwarp; wb < pl.end; wb += P * T) {
+    const unsigned long long t0 = wb + lane;
+    unsigned long long ch[P][W];
+#pragma unroll
+    for (int j = 0; j < P; ++j) {
+      const unsigned long long i = t0 + (unsigned long long)j * T;
+      const bool valid = i < pl.end;
+      unsigned long long B[W];
+#pragma unroll
+      for (int k = 0; k < W; ++k) B[k] = valid ? ldcg64(sB + k * ss + i) : ~0ull;
+      const unsigned long long H = valid ? ldcg64(sH + i) : 0ull;
+      const unsigned int M = valid ? ldcg32(sM + i) : 0u;
+      const unsigned int v1 = M & 0xFFFFu, vt = M >> 16;
+      const unsigned int pj = j * 32 + lane;
+#pragma unroll
+      for (int k = 0; k < W; ++k) {
+        const unsigned long long at = adj[(unsigned long long)vt * W + k];
+        const unsigned long long a1 = adj[(unsigned long long)v1 * W + k];
+        const unsigned long long cand = at & ~B[k];
+        m[j][k] = close_ok ? (cand & a1) : 0ull;
+        ch[j][k] = store ? (cand & ~a1) : 0ull;
+        snb[pj * W + k] = B[k] | at;
+      }
+      sh[pj] = H;
+      sv1[pj] = v1;
+    }
+    list_and_work(false);
+    if (store) {
+#pragma unroll
+      for (int j = 0; j < P; ++j)
+#pragma unroll
+        for (int k = 0; k < W; ++k) m[j][k] = ch[j][k];
+      list_and_work(true);
+    }
+  }
+  block_sum3_u64(nx, ncyc, hacc, s_red);
+  if (tid == 0) {
+    if (nx) atomicAdd(&p.ctl->nxt[s % 3], nx);
+    if (ncyc) atomicAdd(&p.hist[t + 1], ncyc);
+    if (hacc) atomicAdd(p.hash, hacc);
   }
 }
 
@@ -1116,7 +1280,11 @@ __global__ void __launch_bounds__(NT, NT >= 1024 ? 1 : KindTraits<K>::minB) engi
       else if (CAP >= 32 && pl.t <= 32) process_csr_coop<(CAP >= 32 ? 32 : 16)>(p, pl, nrow, ncol, nsig, rtab);
       else process_csr_long(p, pl, nrow, ncol, rtab, s_warp, s_red, &s_base);
     } else {
-      process_bitset<K>(p, pl, adj, rtab, s_warp, s_red, &s_base);
+      // the flattened form for the persistent grid (the small cluster phase keeps the
+      // per-lane form: its levels are small and its 32 warps per block would need 4x the
+      // staging memory)
+      if constexpr (KindTraits<K>::multi || NT >= 1024) process_bitset<K>(p, pl, adj, rtab, s_warp, s_red, &s_base);
+      else process_bitset_flat<K, NT>(p, pl, adj, rtab, s_red);
     }
     if (blockIdx.x == 0 && tid == 0) {
       p.ctl->cnt[(s + 1) % 3] = 0;
