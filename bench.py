@@ -236,7 +236,7 @@ def run_ours(args, work, desc):
                 paths += r.paths
                 eng_ms += r.info.ms_engine
                 eng_bytes += algorithmic_bytes(r)
-                launches += 3  # labelling, seeding, persistent expansion
+                launches += int(r.info.launches)
         torch.cuda.synchronize()
     step_ms = [a.elapsed_time(b) for a, b in ev]
     t_ms = float(sum(step_ms))

@@ -85,11 +85,18 @@ typedef struct cc_options {
   uint32_t mode;               /* CC_MODE_*                                               */
   uint32_t spin_limit;         /* grid-barrier wait limit in polls; 0 = default (~8 s)    */
   uint32_t flags;              /* CC_FLAG_*                                               */
+  uint32_t paths_per_thread;   /* bitset and batch expansion: paths a thread takes per    */
+                               /* round, 1..3; 0 = the build's default for the path       */
+  uint32_t small_phase_paths;  /* bitset graphs: the cluster phase expands levels (or     */
+                               /* chunks) of at most this many paths; 0 = 2 * cluster     */
+                               /* size * 1024                                            */
 } cc_options;
 
 /* cc_options.flags */
 #define CC_FLAG_NO_CLUSTER_PHASE 1u /* bitset graphs: skip the thread-block-cluster phase that  */
                                     /* expands small levels before the persistent grid starts  */
+#define CC_FLAG_NO_GRAPH 2u         /* cc_enumerate: launch every kernel directly instead of    */
+                                    /* replaying the CUDA graph captured by an earlier call    */
 
 /* Build limits. */
 typedef struct cc_limits {
@@ -110,10 +117,12 @@ typedef struct cc_run_info {
   uint32_t mode;           /* CC_MODE_BITSET or CC_MODE_CSR                           */
   uint32_t grid_blocks;    /* persistent grid size                                    */
   uint32_t spilled;        /* 1 if some level was expanded in depth-first chunks      */
-  uint32_t pad;
+  uint32_t launches;       /* kernels this library launched for the call              */
   uint64_t peak_bytes;     /* largest arena extent in use                             */
   int32_t dev_error;       /* device-side error word (0 = none; diagnostics)          */
   int32_t dev_error_info;  /* where it was raised                                     */
+  uint32_t replayed;       /* 1 if the call replayed a captured CUDA graph            */
+  uint32_t pad;
 } cc_run_info;
 
 /* Optional cycle list.  Set the capacities and pointers; the call fills count,
@@ -164,6 +173,14 @@ void cc_graph_free(cc_graph* g);
 cc_status cc_graph_info(const cc_graph* g, uint32_t* n, uint64_t* m, uint32_t* max_degree);
 
 /*
+ * Change the launch options of a context: threads_per_block, blocks_per_sm, mode,
+ * spin_limit, flags, paths_per_thread and small_phase_paths are taken from *opts; the
+ * frontier size, stream and workspace fixed at creation are kept.  Errors: CC_ERR_ARG
+ * (NULL, or a value outside the ranges documented in cc_options).
+ */
+cc_status cc_context_set_options(cc_context* ctx, const cc_options* opts);
+
+/*
  * Enumerate all chordless cycles of a loaded graph with at most max_len vertices.
  *   out_hist    host array of L'+1 entries (L' as above); required
  *   out_hash    host pointer to one uint64; required
@@ -176,6 +193,49 @@ cc_status cc_graph_info(const cc_graph* g, uint32_t* n, uint64_t* m, uint32_t* m
  */
 cc_status cc_enumerate(cc_graph* g, uint32_t max_len, uint64_t* out_hist, uint64_t* out_hash,
                        uint64_t* out_tcount, cc_cycles* out_cycles, cc_run_info* out_info);
+
+/*
+ * CUDA graphs: without out_cycles and without CC_FLAG_NO_GRAPH, the second cc_enumerate of
+ * a graph with the same max_len and launch configuration captures its device work (result
+ * resets, labelling, seeding, the expansion launches and the result copies) into a CUDA
+ * graph kept with the cc_graph, and that call and later ones with the same configuration
+ * replay it with one launch (cc_run_info.replayed).  If capture is not possible the
+ * kernels are launched directly; the results are the same either way.
+ */
+
+/*
+ * Autotuner.  Times candidate launch configurations of cc_enumerate on graph g (all
+ * lengths up to max_len) and returns the fastest:
+ *   bitset or CSR adjacency (when n <= 256), threads_per_block x blocks_per_sm,
+ *   paths_per_thread (bitset), and the cluster phase (off, or small_phase_paths).
+ * Every candidate must give the same histogram and hash as the context's current options;
+ * a mismatch returns CC_ERR_CUDA.  The context's options are restored before returning;
+ * apply the result with cc_context_set_options(ctx, &out->best).
+ *   cache_path  a JSON-lines file (one object per line: device name, graph class, the
+ *               chosen knobs, time), or NULL for no cache.  A line for this device and the
+ *               graph's class (adjacency kind, n and mean degree bucket, L') is returned
+ *               without timing (from_cache = 1); otherwise the search runs and a line is
+ *               appended.
+ *   out->best   the context's options with the tuned knobs set
+ */
+typedef struct cc_tune_result {
+  cc_options best;
+  double ms_best;        /* device time (ms_proc) of the chosen configuration      */
+  double ms_default;     /* of the context's options on entry                      */
+  uint32_t candidates;   /* configurations timed (0 when read from the cache)      */
+  uint32_t from_cache;   /* 1 if read from cache_path                              */
+  char graph_class[64];  /* the cache key's class string                           */
+} cc_tune_result;
+cc_status cc_tune(cc_graph* g, uint32_t max_len, const char* cache_path, cc_tune_result* out);
+
+/*
+ * The same search for cc_batch_submit on the given batch (arguments as there): launch
+ * shape and paths_per_thread, each candidate one whole batch, results compared graph by
+ * graph.  Needs no batch outstanding on the context.
+ */
+cc_status cc_tune_batch(cc_context* ctx, uint32_t count, const uint32_t* n, const uint64_t* row_off,
+                        const uint32_t* row_ptr, const uint64_t* col_off, const uint32_t* col_idx,
+                        uint32_t max_len, const char* cache_path, cc_tune_result* out);
 
 /*
  * Per-step trace of the last cc_enumerate on this context (Section 5, Fig. 4 of the paper

@@ -51,10 +51,13 @@ class cc_options(ctypes.Structure):
         ("mode", ctypes.c_uint32),
         ("spin_limit", ctypes.c_uint32),
         ("flags", ctypes.c_uint32),
+        ("paths_per_thread", ctypes.c_uint32),
+        ("small_phase_paths", ctypes.c_uint32),
     ]
 
 
 CC_FLAG_NO_CLUSTER_PHASE = 1
+CC_FLAG_NO_GRAPH = 2
 
 
 class cc_limits(ctypes.Structure):
@@ -77,10 +80,23 @@ class cc_run_info(ctypes.Structure):
         ("mode", ctypes.c_uint32),
         ("grid_blocks", ctypes.c_uint32),
         ("spilled", ctypes.c_uint32),
-        ("pad", ctypes.c_uint32),
+        ("launches", ctypes.c_uint32),
         ("peak_bytes", ctypes.c_uint64),
         ("dev_error", ctypes.c_int32),
         ("dev_error_info", ctypes.c_int32),
+        ("replayed", ctypes.c_uint32),
+        ("pad", ctypes.c_uint32),
+    ]
+
+
+class cc_tune_result(ctypes.Structure):
+    _fields_ = [
+        ("best", cc_options),
+        ("ms_best", ctypes.c_double),
+        ("ms_default", ctypes.c_double),
+        ("candidates", ctypes.c_uint32),
+        ("from_cache", ctypes.c_uint32),
+        ("graph_class", ctypes.c_char * 64),
     ]
 
 
@@ -119,6 +135,10 @@ SIGNATURES = {
     "cc_batch_poll": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32, _u64p, ctypes.c_uint32,
                                        _u64p, _u64p, _dblp, ctypes.POINTER(cc_run_info)]),
     "cc_get_trace": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_uint32, _u64p, _u64p, _u64p]),
+    "cc_context_set_options": (ctypes.c_int32, [ctypes.c_void_p, ctypes.POINTER(cc_options)]),
+    "cc_tune": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_uint32, ctypes.c_char_p, ctypes.POINTER(cc_tune_result)]),
+    "cc_tune_batch": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_uint32, _u32p, _u64p, _u32p, _u64p, _u32p,
+                                       ctypes.c_uint32, ctypes.c_char_p, ctypes.POINTER(cc_tune_result)]),
     "cc_enumerate_noalloc": (ctypes.c_int32, [ctypes.c_uint32, _u32p, _u32p, ctypes.c_uint32, ctypes.c_void_p,
                                               _u64p, _u64p, _u64p]),
 }
@@ -176,6 +196,33 @@ def cc_context_create(opts: Optional[cc_options] = None) -> ctypes.c_void_p:
 
 def cc_context_destroy(ctx) -> None:
     load_library().cc_context_destroy(ctx)
+
+
+def cc_context_set_options(ctx, opts: cc_options) -> int:
+    return load_library().cc_context_set_options(ctx, ctypes.byref(opts))
+
+
+def _path_arg(path: Optional[str]):
+    return os.fsencode(path) if path else None
+
+
+def cc_tune(g, max_len: int = 0, cache_path: Optional[str] = None):
+    """Returns (status, cc_tune_result)."""
+    out = cc_tune_result()
+    s = load_library().cc_tune(g, max_len, _path_arg(cache_path), ctypes.byref(out))
+    return s, out
+
+
+def cc_tune_batch(ctx, graphs: Sequence, max_len: int = 0, cache_path: Optional[str] = None):
+    """Returns (status, cc_tune_result)."""
+    from .inputs import pack
+    ns, row_off, rp, col_off, cl = pack(graphs)
+    if cl.size == 0:
+        cl = np.zeros(1, dtype=np.uint32)
+    out = cc_tune_result()
+    s = load_library().cc_tune_batch(ctx, len(graphs), _p32(ns), _p64(row_off), _p32(rp), _p64(col_off), _p32(cl),
+                                     max_len, _path_arg(cache_path), ctypes.byref(out))
+    return s, out
 
 
 def cc_graph_load(ctx, n: int, row_ptr: np.ndarray, col_idx: np.ndarray):
@@ -264,7 +311,7 @@ class Context:
 
     def __init__(self, frontier_bytes: int = 0, mode: int = CC_MODE_AUTO, threads_per_block: int = 0,
                  blocks_per_sm: int = 0, spin_limit: int = 0, use_torch: bool = False, stream: int = 0,
-                 flags: int = 0):
+                 flags: int = 0, paths_per_thread: int = 0, small_phase_paths: int = 0):
         self._ws = None
         opts = cc_options()
         opts.frontier_bytes = frontier_bytes
@@ -274,6 +321,8 @@ class Context:
         opts.spin_limit = spin_limit
         opts.stream = stream or None
         opts.flags = flags
+        opts.paths_per_thread = paths_per_thread
+        opts.small_phase_paths = small_phase_paths
         if use_torch:
             import torch
             nbytes = frontier_bytes or (1 << 30)
@@ -300,6 +349,14 @@ class Context:
             self.close()
         except Exception:
             pass
+
+    def set_options(self, opts: cc_options) -> None:
+        _check(cc_context_set_options(self.handle, opts), "cc_context_set_options")
+
+    def tune_batch(self, graphs: Sequence, max_len: int = 0, cache_path: Optional[str] = None) -> cc_tune_result:
+        s, out = cc_tune_batch(self.handle, graphs, max_len, cache_path)
+        _check(s, "cc_tune_batch")
+        return out
 
     def load(self, graph) -> "LoadedGraph":
         s, h = cc_graph_load(self.handle, graph.n, graph.row_ptr, graph.col)
@@ -340,6 +397,11 @@ class LoadedGraph:
                 continue
             _check(s, "cc_enumerate")
             return Result(hist, h, tc, cyc, info)
+
+    def tune(self, max_len: int = 0, cache_path: Optional[str] = None) -> cc_tune_result:
+        s, out = cc_tune(self.handle, max_len, cache_path)
+        _check(s, "cc_tune")
+        return out
 
     def close(self):
         if self.handle:

@@ -21,14 +21,19 @@ using namespace cc;
 
 // ------------------------------------------------------------------ context
 
+static bool options_valid(const cc_options& o) {
+  if (o.threads_per_block && (o.threads_per_block < 64 || o.threads_per_block > 256 || o.threads_per_block % 32))
+    return false;
+  if (o.mode > CC_MODE_CSR || o.blocks_per_sm > 4 || o.paths_per_thread > 3) return false;
+  return true;
+}
+
 extern "C" cc_status cc_context_create(const cc_options* opts, cc_context** out) {
   if (!out) return CC_ERR_ARG;
   *out = nullptr;
   cc_options o{};
   if (opts) o = *opts;
-  if (o.threads_per_block && (o.threads_per_block < 64 || o.threads_per_block > 256 || o.threads_per_block % 32))
-    return CC_ERR_ARG;
-  if (o.mode > CC_MODE_CSR) return CC_ERR_ARG;
+  if (!options_valid(o)) return CC_ERR_ARG;
   int dev = 0;
   CC_CUDA(cudaGetDevice(&dev));
   cudaDeviceProp prop;
@@ -61,6 +66,18 @@ extern "C" cc_status cc_context_create(const cc_options* opts, cc_context** out)
     return CC_ERR_CUDA;
   }
   *out = c;
+  return CC_OK;
+}
+
+extern "C" cc_status cc_context_set_options(cc_context* c, const cc_options* opts) {
+  if (!c || !opts || !options_valid(*opts)) return CC_ERR_ARG;
+  c->opts.threads_per_block = opts->threads_per_block;
+  c->opts.blocks_per_sm = opts->blocks_per_sm;
+  c->opts.mode = opts->mode;
+  c->opts.spin_limit = opts->spin_limit;
+  c->opts.flags = opts->flags;
+  c->opts.paths_per_thread = opts->paths_per_thread;
+  c->opts.small_phase_paths = opts->small_phase_paths;
   return CC_OK;
 }
 
@@ -171,6 +188,7 @@ extern "C" void cc_graph_free(cc_graph* g) {
   dev_free(c, g->d_nrow);
   dev_free(c, g->d_ncol);
   dev_free(c, g->d_nsig);
+  if (g->exec) cudaGraphExecDestroy(g->exec);
   delete g;
 }
 
@@ -262,6 +280,7 @@ extern "C" cc_status cc_enumerate(cc_graph* g, uint32_t max_len, uint64_t* out_h
   p.tcount = d_tcount;
   p.spin_limit = c->opts.spin_limit ? c->opts.spin_limit : kDefaultSpin;
   p.fresh = 1;
+  p.pf = c->opts.paths_per_thread;
   p.seed_entries = (unsigned int)(2 * g->m);
   if (!c->d_trace) {
     if ((s = dev_alloc(c, (void**)&c->d_trace, 16ull * kTraceCap))) {
@@ -322,33 +341,95 @@ extern "C" cc_status cc_enumerate(cc_graph* g, uint32_t max_len, uint64_t* out_h
     if (e == cudaSuccess && x != cudaSuccess) e = x;
     return e == cudaSuccess;
   };
-  ok(cudaEventRecord(c->ev0, st));
-  ok(cudaMemsetAsync(c->ctl, 0, sizeof(Control), st));
-  ok(cudaMemsetAsync(c->d_res, 0, words * 8, st));
-  ok(launch_label_single(g->d_row, g->d_col, n, (unsigned int)(2 * g->m), W, g->d_perm, g->d_adj, g->d_rtab, g->d_nrow, g->d_ncol, g->d_nsig, st));
-  ok(launch_seed_single(kind, p, seed_stride, st));
-  ok(cudaEventRecord(c->ev3, st));
+  // small levels first on one thread-block cluster (hardware barrier between levels),
+  // then the persistent grid resumes from the state it leaves
+  int cs = 0;
   if (!is_csr(kind) && !(c->opts.flags & CC_FLAG_NO_CLUSTER_PHASE)) {
-    // small levels first on one thread-block cluster (hardware barrier between levels),
-    // then the persistent grid resumes from the state it leaves
     const unsigned long long key = (unsigned long long)kind | ((unsigned long long)smem << 8);
-    int cs = -1;
+    cs = -1;
     for (auto& kv : c->cluster_sizes)
       if (kv.first == key) cs = kv.second;
     if (cs < 0) {
       cs = small_cluster_size(kind, smem);
       c->cluster_sizes.push_back({key, cs});
     }
-    if (cs > 0) {
-      ok(launch_small_engine(kind, p, cs, smem, 2ull * cs * 1024, st));
-      p.fresh = 0;
-    }
   }
-  ok(launch_engine(kind, p, grid, block, smem, st));
-  ok(cudaEventRecord(c->ev1, st));
-  ok(cudaMemcpyAsync(c->h_res, c->d_res, words * 8, cudaMemcpyDeviceToHost, st));
-  ok(cudaMemcpyAsync(c->h_ctl, c->ctl, sizeof(Control), cudaMemcpyDeviceToHost, st));
-  ok(cudaEventRecord(c->ev2, st));
+  const unsigned long long handover =
+      c->opts.small_phase_paths ? c->opts.small_phase_paths : 2ull * (cs > 0 ? cs : 0) * 1024;
+  info.launches = 3 + (cs > 0 ? 1 : 0);
+  // the device work of the call, in stream order.  While capturing, events are recorded
+  // as external event nodes so that every replay records them (a plain record in a
+  // capture only orders the captured work).
+  bool capturing = false;
+  auto rec = [&](cudaEvent_t ev) {
+    ok(capturing ? cudaEventRecordWithFlags(ev, st, cudaEventRecordExternal) : cudaEventRecord(ev, st));
+  };
+  auto issue = [&]() {
+    EngineParams q = p;
+    rec(c->ev0);
+    ok(cudaMemsetAsync(c->ctl, 0, sizeof(Control), st));
+    ok(cudaMemsetAsync(c->d_res, 0, words * 8, st));
+    ok(launch_label_single(g->d_row, g->d_col, n, (unsigned int)(2 * g->m), W, g->d_perm, g->d_adj, g->d_rtab,
+                           g->d_nrow, g->d_ncol, g->d_nsig, st));
+    ok(launch_seed_single(kind, q, seed_stride, st));
+    rec(c->ev3);
+    if (cs > 0) {
+      ok(launch_small_engine(kind, q, cs, smem, handover, st));
+      q.fresh = 0;
+    }
+    ok(launch_engine(kind, q, grid, block, smem, st));
+    rec(c->ev1);
+    ok(cudaMemcpyAsync(c->h_res, c->d_res, words * 8, cudaMemcpyDeviceToHost, st));
+    ok(cudaMemcpyAsync(c->h_ctl, c->ctl, sizeof(Control), cudaMemcpyDeviceToHost, st));
+    rec(c->ev2);
+  };
+  // CUDA graph: the key covers everything the captured work depends on
+  const bool use_graph = !out_cycles && !(c->opts.flags & CC_FLAG_NO_GRAPH) && !g->no_graph;
+  unsigned long long gkey = 0;
+  if (use_graph) {
+    const unsigned long long parts[] = {(unsigned long long)kind, (unsigned long long)grid, (unsigned long long)block,
+                                        (unsigned long long)smem, (unsigned long long)cs, handover,
+                                        (unsigned long long)words, (unsigned long long)(uintptr_t)c->h_res,
+                                        (unsigned long long)(uintptr_t)c->h_ctl, (unsigned long long)(uintptr_t)st};
+    gkey = fnv1a(&p, sizeof(p), fnv1a(parts, sizeof(parts)));
+  }
+  if (use_graph && g->exec && g->exec_key == gkey) {
+    ok(cudaGraphLaunch(g->exec, st));
+    info.replayed = 1;
+  } else if (use_graph && g->seen_key != gkey) {
+    // first call with this configuration: launch directly (a graph enumerated once
+    // never pays for a capture)
+    g->seen_key = gkey;
+    issue();
+  } else if (use_graph) {
+    cudaGraph_t gr = nullptr;
+    cudaGraphExec_t ex = nullptr;
+    bool captured = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+    if (captured) {
+      capturing = true;
+      issue();
+      capturing = false;
+      const cudaError_t ce = cudaStreamEndCapture(st, &gr);
+      captured = e == cudaSuccess && ce == cudaSuccess && gr &&
+                 cudaGraphInstantiate(&ex, gr, 0) == cudaSuccess;
+      if (gr) cudaGraphDestroy(gr);
+    }
+    if (captured) {
+      if (g->exec) cudaGraphExecDestroy(g->exec);
+      g->exec = ex;
+      g->exec_key = gkey;
+      ok(cudaGraphLaunch(g->exec, st));
+      info.replayed = 1;
+    } else {
+      // not capturable here: launch directly from now on
+      (void)cudaGetLastError();
+      e = cudaSuccess;
+      g->no_graph = true;
+      issue();
+    }
+  } else {
+    issue();
+  }
   ok(cudaStreamSynchronize(st));
   if (e != cudaSuccess) {
     (void)cudaGetLastError();
@@ -359,9 +440,10 @@ extern "C" cc_status cc_enumerate(cc_graph* g, uint32_t max_len, uint64_t* out_h
     return cuda_status(e);
   }
   float ms1 = 0, ms2 = 0, ms3 = 0;
-  cudaEventElapsedTime(&ms1, c->ev0, c->ev1);
-  cudaEventElapsedTime(&ms2, c->ev0, c->ev2);
-  cudaEventElapsedTime(&ms3, c->ev3, c->ev1);
+  if (cudaEventElapsedTime(&ms1, c->ev0, c->ev1) != cudaSuccess ||
+      cudaEventElapsedTime(&ms2, c->ev0, c->ev2) != cudaSuccess ||
+      cudaEventElapsedTime(&ms3, c->ev3, c->ev1) != cudaSuccess)
+    (void)cudaGetLastError();  // timings stay 0; never leave an error for the caller's next call
   info.ms_engine = ms3;
   const Control& h = *c->h_ctl;
   s = map_dev_err(h.err);
@@ -539,6 +621,7 @@ extern "C" cc_status cc_batch_submit(cc_context* c, uint32_t count, const uint32
   p.step_ts_cap = b.ts_cap;
   p.spin_limit = c->opts.spin_limit ? c->opts.spin_limit : kDefaultSpin;
   p.fresh = 1;
+  p.pf = c->opts.paths_per_thread;
   const unsigned long long seed_stride = round_up(tb_total + 8, 8);
   const unsigned long long seed_bytes = bitset_region_bytes(seed_stride, 1);
   if (seed_bytes > c->arena_bytes / 2) return CC_ERR_CAPACITY;
@@ -629,6 +712,7 @@ extern "C" cc_status cc_batch_poll(cc_context* c, cc_batch_id id, uint32_t timeo
   cc_run_info ri{};
   float ms_eng = 0;
   cudaEventElapsedTime(&ms_eng, c->ev1, c->ev2);
+  (void)cudaGetLastError();  // a failed timing query leaves no error for the caller
   ri.ms_proc = ms_all;
   ri.ms_total = ms_all;
   ri.ms_engine = ms_eng;
@@ -637,6 +721,7 @@ extern "C" cc_status cc_batch_poll(cc_context* c, cc_batch_id id, uint32_t timeo
   ri.peak_bytes = h.peak;
   ri.mode = CC_MODE_BITSET;
   ri.grid_blocks = b.grid;
+  ri.launches = 2;  // labelling + seeding of every graph, one persistent expansion
   // step timestamps are absolute (globaltimer), measured from the engine's start
   const double t_start_ns = (double)h.t_start;
   for (unsigned int g = 0; g < count; ++g) {

@@ -257,7 +257,9 @@ __device__ __forceinline__ void process_bitset(const EngineParams& p, const Step
   const unsigned long long gwarp = ((unsigned long long)(tid >> 5) * gridDim.x + blockIdx.x) * 32ull;
   // the bound is tested on the warp's first thread so every lane runs the same iterations
   // (the body uses full-warp collectives)
-  for (unsigned long long wb = pl.begin + gwarp; wb < pl.end; wb += P * T) {
+  // pf <= P paths per thread per round (a runtime knob; rounds j >= pf are empty)
+  const unsigned int pf = p.pf >= 1 && p.pf <= (unsigned)P ? p.pf : (unsigned)P;
+  for (unsigned long long wb = pl.begin + gwarp; wb < pl.end; wb += pf * T) {
     const unsigned long long t0 = wb + (tid & 31);
     unsigned long long B[P][W], H[P], ch[P][W];
     unsigned int M[P];
@@ -267,7 +269,7 @@ __device__ __forceinline__ void process_bitset(const EngineParams& p, const Step
 #pragma unroll
     for (int j = 0; j < P; ++j) {
       const unsigned long long i = t0 + (unsigned long long)j * T;
-      const bool valid = i < pl.end;
+      const bool valid = (unsigned)j < pf && i < pl.end;
 #pragma unroll
       for (int k = 0; k < W; ++k) B[j][k] = valid ? ldcg64(sB + k * ss + i) : ~0ull;
       H[j] = valid ? ldcg64(sH + i) : 0ull;
@@ -539,13 +541,14 @@ __device__ __forceinline__ void process_bitset_flat(const EngineParams& p, const
     }
   };
 
-  for (unsigned long long wb = pl.begin + gwarp; wb < pl.end; wb += P * T) {
+  const unsigned int pf = p.pf >= 1 && p.pf <= (unsigned)P ? p.pf : (unsigned)P;
+  for (unsigned long long wb = pl.begin + gwarp; wb < pl.end; wb += pf * T) {
     const unsigned long long t0 = wb + lane;
     unsigned long long ch[P][W];
 #pragma unroll
     for (int j = 0; j < P; ++j) {
       const unsigned long long i = t0 + (unsigned long long)j * T;
-      const bool valid = i < pl.end;
+      const bool valid = (unsigned)j < pf && i < pl.end;
       unsigned long long B[W];
 #pragma unroll
       for (int k = 0; k < W; ++k) B[k] = valid ? ldcg64(sB + k * ss + i) : ~0ull;

@@ -82,7 +82,22 @@ struct cc_graph {
   unsigned short* d_ncol = nullptr;
   unsigned long long* d_nsig = nullptr;  // neighbour signatures of the relabelled CSR [2n]
   size_t nrow_bytes = 0, ncol_bytes = 0, adj_bytes = 0, rtab_bytes = 0, nsig_bytes = 0;
+  // captured device work of cc_enumerate for one launch configuration (CUDA graph)
+  cudaGraphExec_t exec = nullptr;
+  unsigned long long exec_key = 0;
+  unsigned long long seen_key = 0;  // configuration of the previous call (captured on repeat)
+  bool no_graph = false;            // capture failed once: launch directly
 };
+
+// FNV-1a over bytes (keys of captured CUDA graphs)
+inline unsigned long long fnv1a(const void* data, size_t bytes, unsigned long long h = 1469598103934665603ull) {
+  const unsigned char* b = static_cast<const unsigned char*>(data);
+  for (size_t i = 0; i < bytes; ++i) {
+    h ^= b[i];
+    h *= 1099511628211ull;
+  }
+  return h;
+}
 
 // ------------------------------------------------------------------ helpers
 

@@ -149,6 +149,8 @@ struct EngineParams {
   unsigned int nsig_bytes;         // CSR staging: bytes of the neighbour signatures
   const unsigned long long* nsig;  // CSR: neighbour signature of each vertex, 2 words [n]
   unsigned long long handover;     // cluster phase: stop before expanding more paths than this
+  unsigned int pf;                 // bitset / batch: paths per thread per round (1..P of the kind)
+  unsigned int pad2_;
 };
 
 #ifdef __CUDACC__

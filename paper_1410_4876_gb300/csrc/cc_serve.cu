@@ -214,6 +214,7 @@ extern "C" cc_status cc_serve_create(cc_context* c, const cc_serve_options* opts
   p.tcount = v->d_tcount;
   p.live = v->d_live;
   p.spin_limit = c->opts.spin_limit ? c->opts.spin_limit : kDefaultSpin;
+  p.pf = c->opts.paths_per_thread;
   p.fresh = 0;
   p.max_steps = o.steps_per_round;
   p.reserve = o.reserve_paths;

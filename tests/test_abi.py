@@ -43,3 +43,33 @@ def test_status_strings_and_limits():
     assert cc.status_str(cc.CC_ERR_INVALID_GRAPH) == "not a simple undirected graph"
     lim = cc.cc_get_limits()
     assert lim.max_n_bitset == 256 and lim.max_n_batch == 64 and lim.max_n_csr >= 2000
+
+
+def test_struct_layouts_match_header(tmp_path):
+    # the ctypes mirrors of the option, result and tuner structs have the C layout
+    import shutil
+    import subprocess
+
+    from paper_1410_4876_gb300 import cc
+    gcc = shutil.which("gcc") or shutil.which("cc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    structs = {"cc_options": cc.cc_options, "cc_run_info": cc.cc_run_info, "cc_tune_result": cc.cc_tune_result,
+               "cc_cycles": cc.cc_cycles, "cc_serve_options": cc.cc_serve_options,
+               "cc_completion": cc.cc_completion}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "cc.h"', "int main(void) {"]
+    for name, py in structs.items():
+        lines.append(f'  printf("{name} size %zu\\n", sizeof({name}));')
+        for f, _ in py._fields_:
+            lines.append(f'  printf("{name} {f} %zu\\n", offsetof({name}, {f}));')
+    lines.append("  return 0;\n}")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run([gcc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    for line in filter(None, out):
+        name, field, value = line.split()
+        py = structs[name]
+        got = ctypes.sizeof(py) if field == "size" else getattr(py, field).offset
+        assert got == int(value), (name, field, got, value)
