@@ -35,6 +35,10 @@ WORKLOADS = {
                     "all chordless cycles of every length", lambda: [(I.grid(8, 8), 0), (I.gnp(60, 0.15, 7), 0)]),
     "grid6": ("grid 6x6 (36 vertices, 60 edges), all lengths", lambda: [(I.grid(6, 6), 0)]),
     "gnm2000": ("G(n=2000, m=4000, seed 11), cycles up to 12 vertices", lambda: [(I.gnm(2000, 4000, 11), 12)]),
+    # the largest synthetic rows of Table 1, for comparison with the paper's own timings
+    "grid7x10": ("grid 7x10 (70 vertices, 123 edges), all lengths", lambda: [(I.grid(7, 10), 0)]),
+    "grid8x10": ("grid 8x10 (80 vertices, 142 edges), all lengths (Table 1's count-only row)",
+                 lambda: [(I.grid(8, 10), 0)]),
 }
 
 
@@ -206,7 +210,8 @@ def run_ours(args, work, desc):
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
     # run on torch's stream so events, the L2 flush and the library share one stream
-    ctx = cc.Context(frontier_bytes=args.frontier_mb << 20, stream=stream.cuda_stream)
+    ctx = cc.Context(frontier_bytes=_frontier_bytes(args, 8 << 10), stream=stream.cuda_stream,
+                     flags=cc.CC_FLAG_NO_GRAPH if args.no_graph else 0)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # twice the 129 MB L2
     loaded = [(ctx.load(g), L, g) for g, L in work]
 
@@ -310,6 +315,10 @@ def _percentiles(x):
     return float(np.percentile(x, 50)), float(np.percentile(x, 99))
 
 
+def _frontier_bytes(args, default_mb):
+    return (args.frontier_mb or default_mb) << 20
+
+
 def run_batch(args):
     """4096 graphs of the batch mixture (seed 0) in one persistent launch, against plain
     per-graph cc_enumerate calls of the same graphs."""
@@ -317,7 +326,7 @@ def run_batch(args):
 
     from paper_1410_4876_gb300 import cc
     graphs = I.mixture(args.batch_count, 0)
-    ctx = cc.Context(frontier_bytes=args.frontier_mb << 20)
+    ctx = cc.Context(frontier_bytes=_frontier_bytes(args, 64 << 10))
     for _ in range(args.warmup):
         ctx.batch(graphs[:256])
     torch.cuda.synchronize()
@@ -348,7 +357,7 @@ def run_batch(args):
         "config": {"workload": f"{len(graphs)} graphs of the seeded batch mixture (50% G(n,p), 30% grids, "
                                "20% K_ab), all lengths", "cycles": cyc, "paths": paths},
         "paths_expanded_per_s": paths / t, "engine_ms": eng_ms, "spilled": int(last_info.spilled),
-        "peak_frontier_bytes": int(last_info.peak_bytes), "frontier_bytes": args.frontier_mb << 20,
+        "peak_frontier_bytes": int(last_info.peak_bytes), "frontier_bytes": _frontier_bytes(args, 64 << 10),
         "per_graph_done_ms": {"p50": p50, "p99": p99},
         "per_graph_launches": {"value": seq_cyc / t_seq, "unit": "cycles/s", "seconds": t_seq},
         "batched_over_per_graph": (cyc / t) / (seq_cyc / t_seq),
@@ -365,7 +374,7 @@ def run_serve(args):
     arrivals = I.poisson_arrivals(args.rate, args.serve_seconds, 3)
     reqs = [I.make(*I.serving_request(i, 3)) for i in range(len(arrivals))]
     n_req = len(reqs)
-    ctx = cc.Context(frontier_bytes=args.frontier_mb << 20)
+    ctx = cc.Context(frontier_bytes=_frontier_bytes(args, 64 << 10))
     srv = cc.Server(ctx, slots=4096, steps_per_round=args.serve_steps, admit_bytes=64 << 30)
     # warm up the kernels on a few requests
     for g in reqs[:8]:
@@ -457,7 +466,11 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="grid8+gnp60", choices=sorted(WORKLOADS) + ["batch", "serve"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the cpu_baseline leg")
-    ap.add_argument("--frontier-mb", type=int, default=8192, help="device memory for paths in flight (MiB)")
+    ap.add_argument("--frontier-mb", type=int, default=0,
+                    help="device memory for paths in flight (MiB); 0 = 8 GiB for single graphs, "
+                         "64 GiB for the batch and serving workloads (whose frontiers hold many graphs)")
+    ap.add_argument("--no-graph", action="store_true",
+                    help="launch every kernel directly (no CUDA-graph replay of repeated enumerations)")
     ap.add_argument("--batch-count", type=int, default=4096)
     ap.add_argument("--rate", type=float, default=2000.0, help="serving: mean arrivals per second")
     ap.add_argument("--serve-seconds", type=float, default=10.0, help="serving: arrival window (s)")

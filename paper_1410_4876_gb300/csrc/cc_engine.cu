@@ -585,6 +585,175 @@ __device__ __forceinline__ void process_bitset_flat(const EngineParams& p, const
   }
 }
 
+// The batch form of the flattened expansion (records of many graphs in one frontier; M
+// holds v1, vt, t and the graph's slot g, whose rows and r-table sit at g * 64).  Per-path
+// statistics (paths expanded, children and closings per (slot, length)) are accumulated
+// in lane order as runs of one key, as in the per-lane form; a closing's hash is added to
+// its slot's sum by one atomic per distinct slot among the lanes of a round.
+template <int NT>
+__device__ __forceinline__ void process_multi_flat(const EngineParams& p, const StepPlan& pl,
+                                                   const unsigned long long* adj, const unsigned long long* rtab) {
+  constexpr int P = KindTraits<Kind::Multi>::P;
+  constexpr unsigned int CL = FlatSmem<1, P, NT>::CL;
+  __shared__ FlatSmem<1, P, NT> fs;
+  const unsigned int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  unsigned long long* snb = fs.nb[wid];
+  unsigned long long* sh = fs.h[wid];
+  unsigned int* smeta = fs.v1[wid];  // v1 | t << 6 | g << 12
+  unsigned int* sl = fs.list[wid];
+  const unsigned long long ss = pl.src_stride, ds = pl.dst_stride;
+  const unsigned long long* sB = reinterpret_cast<const unsigned long long*>(p.arena + pl.src_base);
+  const unsigned long long* sH = sB + ss;
+  const unsigned int* sM = reinterpret_cast<const unsigned int*>(sH + ss);
+  unsigned long long* dB = reinterpret_cast<unsigned long long*>(p.arena + pl.dst_base);
+  unsigned long long* dH = dB + ds;
+  unsigned int* dM = reinterpret_cast<unsigned int*>(dH + ds);
+  const bool store = ds != 0;
+  const unsigned long long s = pl.s;
+  unsigned long long nx = 0;
+  StatRun run;
+  run.key = 0xFFFFFFFFu;
+  const unsigned long long T = (unsigned long long)gridDim.x * blockDim.x;
+  const unsigned long long gwarp = ((unsigned long long)wid * gridDim.x + blockIdx.x) * 32ull;
+
+  auto flush_children = [&](unsigned int n) {
+    __syncwarp();
+    unsigned long long base = 0;
+    if (lane == 0) base = atomicAdd(&p.ctl->cnt[s % 3], (unsigned long long)n);
+    base = __shfl_sync(0xffffffffu, base, 0);
+    for (unsigned int i = lane; i < n; i += 32) {
+      const unsigned int e = sl[i], pj = e >> 8, v = e & 0xFFu;
+      const unsigned int meta = smeta[pj], v1 = meta & 63u, tt = (meta >> 6) & 63u, g = meta >> 12;
+      const unsigned long long go = (unsigned long long)g * 64ull, slot = base + i;
+      if (slot < ds) {
+        const unsigned long long nb = snb[pj];
+        dB[slot] = nb;
+        dH[slot] = sh[pj] + __ldg(rtab + go + v);
+        dM[slot] = v1 | (v << 6) | ((tt + 1) << 12) | (g << 18);
+        if (tt + 2 < p.Lg[g]) nx += __popcll(__ldg(adj + go + v) & ~nb & ~__ldg(adj + go + v1));
+      } else {
+        set_err(p.ctl, kDevBounds, 1);
+      }
+    }
+    __syncwarp();
+  };
+  auto flush_closings = [&](unsigned int n) {
+    __syncwarp();
+    for (unsigned int r0 = 0; r0 < n; r0 += 32) {
+      const unsigned int i = r0 + lane;
+      unsigned int g = 0xFFFFFFFFu;
+      unsigned long long h = 0;
+      if (i < n) {
+        const unsigned int e = sl[i], pj = e >> 8, v = e & 0xFFu;
+        const unsigned int meta = smeta[pj], tt = (meta >> 6) & 63u;
+        g = meta >> 12;
+        h = mix64(sh[pj] + __ldg(rtab + (unsigned long long)g * 64ull + v) + (unsigned long long)(tt + 1) * kGamma);
+      }
+      // one atomic per distinct slot among the lanes
+      const unsigned int grp = __match_any_sync(0xffffffffu, g);
+      unsigned long long sum = 0;
+      for (unsigned int m = grp; m; m &= m - 1) sum += __shfl_sync(grp, h, __ffs(m) - 1);
+      if (g != 0xFFFFFFFFu && lane == (unsigned)(__ffs(grp) - 1)) atomicAdd(&p.hash[g], sum);
+    }
+    __syncwarp();
+  };
+  unsigned long long m[P];
+  auto list_and_work = [&](bool children) {
+    unsigned int cnt = 0;
+#pragma unroll
+    for (int j = 0; j < P; ++j) cnt += __popcll(m[j]);
+    unsigned int incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned int y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= (unsigned)o) incl += y;
+    }
+    const unsigned int excl = incl - cnt, total = __shfl_sync(0xffffffffu, incl, 31);
+    for (unsigned int c0 = 0; c0 < total; c0 += CL) {
+      if (cnt && excl < c0 + CL && excl + cnt > c0) {
+        unsigned int idx = excl;
+#pragma unroll
+        for (int j = 0; j < P; ++j) {
+          unsigned long long b = m[j];
+          while (b) {
+            const unsigned int v = __ffsll((long long)b) - 1;
+            b &= b - 1;
+            if (idx >= c0 && idx < c0 + CL) sl[idx - c0] = (unsigned int)(j * 32 + lane) << 8 | v;
+            ++idx;
+          }
+        }
+      }
+      if (children) flush_children(min(CL, total - c0));
+      else flush_closings(min(CL, total - c0));
+    }
+  };
+
+  const unsigned int pf = p.pf >= 1 && p.pf <= (unsigned)P ? p.pf : (unsigned)P;
+  for (unsigned long long wb = pl.begin + gwarp; wb < pl.end; wb += pf * T) {
+    const unsigned long long t0 = wb + lane;
+    unsigned long long ch[P];
+    unsigned int key[P], nc[P], nk[P];
+#pragma unroll
+    for (int j = 0; j < P; ++j) {
+      const unsigned long long i = t0 + (unsigned long long)j * T;
+      const bool valid = (unsigned)j < pf && i < pl.end;
+      const unsigned long long B = valid ? ldcg64(sB + i) : ~0ull;
+      const unsigned long long H = valid ? ldcg64(sH + i) : 0ull;
+      const unsigned int M = valid ? ldcg32(sM + i) : 0u;
+      const unsigned int v1 = M & 63u, vt = (M >> 6) & 63u, tt = (M >> 12) & 63u, g = M >> 18;
+      const unsigned long long go = (unsigned long long)g * 64ull;
+      const unsigned int Lr = valid ? p.Lg[g] : 0u;
+      const unsigned long long at = __ldg(adj + go + vt), a1 = __ldg(adj + go + v1);
+      const unsigned long long cand = at & ~B;
+      m[j] = (tt + 1 <= Lr) ? (cand & a1) : 0ull;
+      ch[j] = (store && tt + 1 < Lr) ? (cand & ~a1) : 0ull;
+      const unsigned int pj = j * 32 + lane;
+      snb[pj] = B | at;
+      sh[pj] = H;
+      smeta[pj] = v1 | (tt << 6) | (g << 12);
+      key[j] = valid ? (g << 6 | tt) : 0xFFFFFFFFu;
+      nc[j] = __popcll(m[j]);
+      nk[j] = __popcll(ch[j]);
+    }
+    // per (slot, length) counts, as runs of one key (no hash here: closings add theirs)
+#pragma unroll
+    for (int j = 0; j < P; ++j) {
+      const unsigned int k = key[j];
+      const bool v = k != 0xFFFFFFFFu;
+      const bool m0 = v && k == run.key;
+      if (m0) run.add(nc[j], nk[j], 0ull);
+      const unsigned int rest = __ballot_sync(0xffffffffu, v && !m0);
+      if (rest) {
+        run.flush(p, s);
+        run.key = __shfl_sync(0xffffffffu, k, 31 - __clz(rest));
+        const bool m1 = v && !m0 && k == run.key;
+        if (m1) run.add(nc[j], nk[j], 0ull);
+        unsigned int pending = __ballot_sync(0xffffffffu, v && !m0 && !m1);
+        while (pending) {
+          const int leader = __ffs(pending) - 1;
+          const unsigned int lk = __shfl_sync(0xffffffffu, k, leader);
+          const bool mine = k == lk;
+          const unsigned int grp = __ballot_sync(0xffffffffu, mine);
+          StatRun one;
+          one.key = lk;
+          if (mine) one.add(nc[j], nk[j], 0ull);
+          one.flush(p, s);
+          pending &= ~grp;
+        }
+      }
+    }
+    list_and_work(false);
+    if (store) {
+#pragma unroll
+      for (int j = 0; j < P; ++j) m[j] = ch[j];
+      list_and_work(true);
+    }
+  }
+  run.flush(p, s);
+  const unsigned long long tot = warp_sum_u64(nx);
+  if (lane == 0 && tot) atomicAdd(&p.ctl->nxt[s % 3], tot);
+}
+
 // ------------------------------------------------------------------ CSR expansion
 
 // CSR records: the path's relabelled ids in order, as u16, padded with 0xFFFF (never a
@@ -1286,7 +1455,8 @@ __global__ void __launch_bounds__(NT, NT >= 1024 ? 1 : KindTraits<K>::minB) engi
       // the flattened form for the persistent grid (the small cluster phase keeps the
       // per-lane form: its levels are small and its 32 warps per block would need 4x the
       // staging memory)
-      if constexpr (KindTraits<K>::multi || NT >= 1024) process_bitset<K>(p, pl, adj, rtab, s_warp, s_red, &s_base);
+      if constexpr (NT >= 1024) process_bitset<K>(p, pl, adj, rtab, s_warp, s_red, &s_base);
+      else if constexpr (KindTraits<K>::multi) process_multi_flat<NT>(p, pl, adj, rtab);
       else process_bitset_flat<K, NT>(p, pl, adj, rtab, s_red);
     }
     if (blockIdx.x == 0 && tid == 0) {

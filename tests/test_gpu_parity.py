@@ -72,6 +72,15 @@ def test_grid6x10_table1(ctx):
     assert r.total == 800139  # Table 1
 
 
+@pytest.mark.parametrize("k,l,total", [(7, 10, 8136453), (8, 10, 71535910)])
+def test_large_grids_table1(ctx, k, l, total):
+    # the two largest synthetic rows of Table 1 (no triangles in a grid, so the total is
+    # the printed #clc); the 8x10 row is the paper's count-only run
+    r = ctx.enumerate(I.grid(k, l))
+    assert r.total == total
+    assert int(r.hist[3]) == 0 and int(r.hist[4]) == (k - 1) * (l - 1)
+
+
 @pytest.mark.parametrize("max_len", [1, 2, 3, 4, 5, 8, 13])
 def test_length_bound(ctx, max_len):
     for g in [I.grid(5, 5), I.gnp(40, 0.12, 3), I.wheel(12), I.gnp(150, 0.022, 9)]:
