@@ -614,7 +614,6 @@ __device__ __forceinline__ void process_multi_flat(const EngineParams& p, const 
   StatRun run;
   run.key = 0xFFFFFFFFu;
   const unsigned long long T = (unsigned long long)gridDim.x * blockDim.x;
-  const unsigned long long gwarp = ((unsigned long long)wid * gridDim.x + blockIdx.x) * 32ull;
 
   auto flush_children = [&](unsigned int n) {
     __syncwarp();
@@ -688,14 +687,17 @@ __device__ __forceinline__ void process_multi_flat(const EngineParams& p, const 
     }
   };
 
+  // a warp takes pf * 32 consecutive records per round (a frontier keeps each graph's
+  // records together, so the per-slot statistics of a round are mostly one run)
   const unsigned int pf = p.pf >= 1 && p.pf <= (unsigned)P ? p.pf : (unsigned)P;
+  const unsigned long long gwarp = ((unsigned long long)wid * gridDim.x + blockIdx.x) * 32ull * pf;
   for (unsigned long long wb = pl.begin + gwarp; wb < pl.end; wb += pf * T) {
     const unsigned long long t0 = wb + lane;
     unsigned long long ch[P];
     unsigned int key[P], nc[P], nk[P];
 #pragma unroll
     for (int j = 0; j < P; ++j) {
-      const unsigned long long i = t0 + (unsigned long long)j * T;
+      const unsigned long long i = t0 + (unsigned long long)j * 32ull;
       const bool valid = (unsigned)j < pf && i < pl.end;
       const unsigned long long B = valid ? ldcg64(sB + i) : ~0ull;
       const unsigned long long H = valid ? ldcg64(sH + i) : 0ull;
@@ -1469,9 +1471,12 @@ __global__ void __launch_bounds__(NT, NT >= 1024 ? 1 : KindTraits<K>::minB) engi
       break;
     }
     if (tid == 0) {
+      // the step's counters and the error word, in one round trip
       const unsigned long long c = ld_relaxed_u64(&p.ctl->cnt[s % 3]);
       const unsigned long long nx = ld_relaxed_u64(&p.ctl->nxt[s % 3]);
+      const int err = ld_relaxed_i32(&p.ctl->err);
       commit_step<K>(p, st, c, nx, blockIdx.x == 0);
+      if (err != 0) st.depth = 0;  // every block reads the same word: all stop here
       if (blockIdx.x == 0 && p.step_ts && s < p.step_ts_cap) {
         p.step_ts[s] = globaltimer();
         if (p.step_rec) p.step_rec[s] = st.chunk;
