@@ -42,17 +42,38 @@ WORKLOADS = {
 }
 
 
-def algorithmic_bytes(r) -> int:
+def unstored_levels(tcount, expanded) -> set:
+    """Levels that two-level steps expanded without storing them, from the per-step trace
+    (a step expands one level, or a level and its children; chunked steps of a spilled run
+    are not resolved and count every level as stored)."""
+    nz = [t for t in range(len(tcount)) if tcount[t]]
+    skip, i = set(), 0
+    for e in (int(x) for x in expanded):
+        if i < len(nz) and e == int(tcount[nz[i]]):
+            i += 1
+        elif i + 1 < len(nz) and e == int(tcount[nz[i]]) + int(tcount[nz[i + 1]]):
+            skip.add(nz[i + 1])
+            i += 2
+        else:
+            return set()
+    return skip if i == len(nz) else set()
+
+
+def algorithmic_bytes(r, n: int, skip=()) -> int:
     """Bytes the expansion kernel must move: every stored path is read once and every
-    path after the initial triplets is written once.  Record sizes: bitset, n <= 64:
+    stored path after the initial triplets is written once (levels in `skip` were expanded
+    inside a two-level step and never stored).  Record sizes: bitset, n <= 64:
     B (8) + H (8) + M (4) = 20 bytes; n <= 128: 28; n <= 256: 44; CSR: the path's u16 ids
     padded to a multiple of 8 (16 bytes for t <= 8, 32 for t <= 16, ...)."""
-    tc = r.tcount
+    tc = r.tcount.astype(np.int64).copy()
+    if tc.size <= 3:
+        return 0
+    for t in skip:
+        tc[t] = 0
     if r.info.mode == 2:
         t = np.arange(tc.size, dtype=np.int64)
         rec = (t + 7) // 8 * 16
-        return int((tc.astype(np.int64) * rec).sum() * 2 - int(tc[3]) * 16) if tc.size > 3 else 0
-    n = len(r.hist) - 1
+        return int((tc * rec).sum() * 2 - int(tc[3]) * 16)
     rec = 20 if n <= 64 else (28 if n <= 128 else 44)
     return rec * (2 * int(tc.sum()) - int(tc[3]))
 
@@ -240,9 +261,13 @@ def run_ours(args, work, desc):
                 cycles += r.total
                 paths += r.paths
                 eng_ms += r.info.ms_engine
-                eng_bytes += algorithmic_bytes(r)
                 launches += int(r.info.launches)
         torch.cuda.synchronize()
+    # algorithmic bytes per step: the stored levels of each graph, from one more call's trace
+    for lg, L, g in loaded:
+        r = lg.enumerate(L)
+        _, expanded = cc.cc_get_trace(ctx.handle)
+        eng_bytes += args.steps * algorithmic_bytes(r, g.n, unstored_levels(r.tcount, expanded))
     step_ms = [a.elapsed_time(b) for a, b in ev]
     t_ms = float(sum(step_ms))
     if dist:

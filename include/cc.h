@@ -97,6 +97,10 @@ typedef struct cc_options {
                                     /* expands small levels before the persistent grid starts  */
 #define CC_FLAG_NO_GRAPH 2u         /* cc_enumerate: launch every kernel directly instead of    */
                                     /* replaying the CUDA graph captured by an earlier call    */
+#define CC_FLAG_NO_FUSE 4u          /* bitset graphs: expand one level per grid step (by       */
+                                    /* default a level whose children are known exactly and    */
+                                    /* fit is expanded together with its children, and only    */
+                                    /* the grandchildren are stored)                           */
 
 /* Build limits. */
 typedef struct cc_limits {
@@ -207,7 +211,8 @@ cc_status cc_enumerate(cc_graph* g, uint32_t max_len, uint64_t* out_hist, uint64
  * Autotuner.  Times candidate launch configurations of cc_enumerate on graph g (all
  * lengths up to max_len) and returns the fastest:
  *   bitset or CSR adjacency (when n <= 256), threads_per_block x blocks_per_sm,
- *   paths_per_thread (bitset), and the cluster phase (off, or small_phase_paths).
+ *   paths_per_thread (bitset), the cluster phase (off, or small_phase_paths) and
+ *   two-level steps (CC_FLAG_NO_FUSE).
  * Every candidate must give the same histogram and hash as the context's current options;
  * a mismatch returns CC_ERR_CUDA.  The context's options are restored before returning;
  * apply the result with cc_context_set_options(ctx, &out->best).

@@ -58,6 +58,7 @@ class cc_options(ctypes.Structure):
 
 CC_FLAG_NO_CLUSTER_PHASE = 1
 CC_FLAG_NO_GRAPH = 2
+CC_FLAG_NO_FUSE = 4
 
 
 class cc_limits(ctypes.Structure):

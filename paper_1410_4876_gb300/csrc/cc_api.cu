@@ -281,6 +281,7 @@ extern "C" cc_status cc_enumerate(cc_graph* g, uint32_t max_len, uint64_t* out_h
   p.spin_limit = c->opts.spin_limit ? c->opts.spin_limit : kDefaultSpin;
   p.fresh = 1;
   p.pf = c->opts.paths_per_thread;
+  p.fuse_ok = (!is_csr(kind) && !(c->opts.flags & CC_FLAG_NO_FUSE)) ? 1u : 0u;
   p.seed_entries = (unsigned int)(2 * g->m);
   if (!c->d_trace) {
     if ((s = dev_alloc(c, (void**)&c->d_trace, 16ull * kTraceCap))) {

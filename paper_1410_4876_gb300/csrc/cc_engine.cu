@@ -25,13 +25,16 @@ struct StepPlan {
   unsigned long long s;
   unsigned int t;
   unsigned int done;
+  unsigned int fuse;  // 1: expand levels t and t+1 in this step, store level t+2
+  unsigned int pad_;
 };
 
 struct LocalState {
   Frame cur;
   Frame child;
   unsigned long long bot, top, chunk, peak;
-  unsigned int depth, has_child, gen;
+  unsigned int depth, has_child, gen, fused;
+  unsigned long long expanded;  // paths expanded by the planned step (both levels of a fused one)
 };
 
 __device__ __forceinline__ Frame load_frame(const Frame* f) {
@@ -63,6 +66,8 @@ struct KindTraits {
   // paths per thread per round of the flattened single-graph form (one slot atomic per
   // warp per round)
   static constexpr int PF = K == Kind::Bitset1 ? 3 : (K == Kind::Bitset2 ? 2 : 1);
+  // children staged per batch in a two-level step, in rounds of 32 (shared memory bound)
+  static constexpr int PF2 = K == Kind::Bitset1 ? 2 : 1;
 };
 
 template <Kind K>
@@ -102,6 +107,44 @@ __device__ bool plan_step(const EngineParams& p, LocalState& st, StepPlan& pl) {
   unsigned long long cap = need + (need || res ? res : 0ull);
   st.chunk = rem;
   st.has_child = 0;
+  st.fused = 0;
+  pl.fuse = 0;
+  if constexpr (!KindTraits<K>::multi && !KindTraits<K>::csr) {
+    // Two levels in one step: a whole frame whose children (level t+1) are known exactly
+    // is expanded, its children are expanded in the same step without being stored, and
+    // only the grandchildren (level t+2) are stored.  Their count is bounded by
+    // children * maxch; the step is taken only when that bound fits the free arena
+    // (otherwise the level runs alone and may be split into depth-first chunks), and
+    // only while the frontier grows by at most 1.3x per level (measured: steps of
+    // fast-growing levels are quicker one level at a time).
+    if (p.fuse_ok && !p.cluster && t + 1 < p.L && f.cursor == 0 && f.next != kNoNext && f.next > 0 &&
+        f.next * 10ull <= f.count * 13ull) {
+      const unsigned long long need2 = (t + 2 < p.L) ? f.next * p.maxch : 0ull;
+      const unsigned long long rb2 = record_bytes<K>(t + 2);
+      const unsigned long long freeb = st.top - st.bot;
+      const unsigned long long maxcap2 = freeb > 1024 ? ((freeb - 1024) / rb2) & ~7ull : 0ull;
+      if (need2 <= maxcap2) {
+        st.fused = 1;
+        pl.fuse = 1;
+        if (need2 > 0) {
+          const unsigned long long stride = round_up(need2, 8);
+          const unsigned long long bytes = region_bytes<K>(stride, t + 2);
+          Frame& c = st.child;
+          c.end = 1u - f.end;
+          c.base = c.end ? st.top - bytes : st.bot;
+          c.bytes = bytes;
+          c.stride = stride;
+          c.count = 0;
+          c.cursor = 0;
+          c.next = kNoNext;
+          c.t = t + 2;
+          st.has_child = 1;
+          st.peak = max(st.peak, p.arena_bytes - (freeb - bytes));
+        }
+        cap = 0;  // the single-level plan below is not used
+      }
+    }
+  }
   if (cap > 0) {
     const unsigned long long rb = record_bytes<K>(t + 1);
     const unsigned long long freeb = st.top - st.bot;
@@ -140,6 +183,7 @@ __device__ bool plan_step(const EngineParams& p, LocalState& st, StepPlan& pl) {
     st.has_child = 1;
     st.peak = max(st.peak, p.arena_bytes - (freeb - bytes));
   }
+  st.expanded = st.chunk + (st.fused ? f.next : 0ull);
   pl.src_base = f.base;
   pl.src_stride = f.stride;
   pl.begin = f.cursor;
@@ -154,6 +198,8 @@ template <Kind K>
 __device__ void commit_step(const EngineParams& p, LocalState& st, unsigned long long c, unsigned long long nx,
                             bool writer) {
   const unsigned int t = st.cur.t;
+  // a two-level step: its children were counted exactly before the step (the frame's next)
+  if (st.fused && writer) atomicAdd(&p.tcount[t + 1], st.cur.next);
   st.cur.cursor += st.chunk;
   const bool consumed = st.cur.cursor >= st.cur.count;
   if (consumed) {
@@ -174,7 +220,7 @@ __device__ void commit_step(const EngineParams& p, LocalState& st, unsigned long
     }
     if (writer) {
       store_frame(&p.frames[st.depth], g);
-      if constexpr (!KindTraits<K>::multi) atomicAdd(&p.tcount[t + 1], c);
+      if constexpr (!KindTraits<K>::multi) atomicAdd(&p.tcount[g.t], c);
     }
     st.depth += 1;
     st.cur = g;
@@ -440,6 +486,12 @@ struct FlatSmem {
   unsigned int list[NT / 32][CL];              // entries: path << 8 | v
 };
 
+template <int W, int P, int NT>
+__device__ __forceinline__ FlatSmem<W, P, NT>& flat_smem() {
+  __shared__ FlatSmem<W, P, NT> fs;
+  return fs;
+}
+
 template <Kind K, int NT>
 __device__ __forceinline__ void process_bitset_flat(const EngineParams& p, const StepPlan& pl,
                                                     const unsigned long long* adj, const unsigned long long* rtab,
@@ -447,7 +499,7 @@ __device__ __forceinline__ void process_bitset_flat(const EngineParams& p, const
   constexpr int W = KindTraits<K>::W;
   constexpr int P = KindTraits<K>::PF;
   constexpr unsigned int CL = FlatSmem<W, P, NT>::CL;
-  __shared__ FlatSmem<W, P, NT> fs;
+  FlatSmem<W, P, NT>& fs = flat_smem<W, P, NT>();
   const unsigned int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   unsigned long long* snb = fs.nb[wid];
   unsigned long long* sh = fs.h[wid];
@@ -581,6 +633,244 @@ __device__ __forceinline__ void process_bitset_flat(const EngineParams& p, const
   if (tid == 0) {
     if (nx) atomicAdd(&p.ctl->nxt[s % 3], nx);
     if (ncyc) atomicAdd(&p.hist[t + 1], ncyc);
+    if (hacc) atomicAdd(p.hash, hacc);
+  }
+}
+
+// Two levels in one step (single graph, bitset).  Level t is expanded as in the flattened
+// form, but every candidate (closing or child) is listed once; the list is worked off P*32
+// entries at a time: a candidate adjacent to v1 closes a cycle of t+1 vertices, any other
+// is a child of level t+1, which is not stored but staged in shared memory with its
+// blocked set B | Adj(vt) | Adj(v), H + r(v) and its closing / child masks.  The staged
+// children (P2 rounds of 32 at a time) are then expanded in the flattened way, and only
+// their children (level t+2) are stored, with their exact child counts summed for the
+// next frame.
+template <int W, int P, int NT>
+struct FusedSmem {
+  unsigned long long nb[NT / 32][P * 32 * W];  // staged children: blocked set of their children
+  unsigned long long h[NT / 32][P * 32];       // their H'
+  unsigned long long cl[NT / 32][P * 32 * W];  // closing mask (cycles of t+2 vertices)
+  unsigned long long ch[NT / 32][P * 32 * W];  // child mask (stored paths of t+2 vertices)
+  unsigned int v1[NT / 32][P * 32];
+  unsigned int list[NT / 32][64 * P];  // level t+2 entries: slot << 8 | w
+};
+
+template <Kind K, int NT>
+__device__ __forceinline__ void process_bitset_fused(const EngineParams& p, const StepPlan& pl,
+                                                     const unsigned long long* adj, const unsigned long long* rtab,
+                                                     unsigned long long* s_red) {
+  constexpr int W = KindTraits<K>::W;
+  constexpr int P = KindTraits<K>::PF, P2 = KindTraits<K>::PF2;
+  constexpr unsigned int CL = FlatSmem<W, P, NT>::CL, CL2 = 64 * P2;
+  FlatSmem<W, P, NT>& fs = flat_smem<W, P, NT>();
+  __shared__ FusedSmem<W, P2, NT> fs2;
+  const unsigned int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  unsigned long long* snb = fs.nb[wid];
+  unsigned long long* sh = fs.h[wid];
+  unsigned int* sv1 = fs.v1[wid];
+  unsigned int* sl = fs.list[wid];
+  unsigned long long* snb2 = fs2.nb[wid];
+  unsigned long long* sh2 = fs2.h[wid];
+  unsigned long long* scl2 = fs2.cl[wid];
+  unsigned long long* sch2 = fs2.ch[wid];
+  unsigned int* sv12 = fs2.v1[wid];
+  unsigned int* sl2 = fs2.list[wid];
+  const unsigned long long ss = pl.src_stride, ds = pl.dst_stride;
+  const unsigned long long* sB = reinterpret_cast<const unsigned long long*>(p.arena + pl.src_base);
+  const unsigned long long* sH = sB + W * ss;
+  const unsigned int* sM = reinterpret_cast<const unsigned int*>(sH + ss);
+  unsigned long long* dB = reinterpret_cast<unsigned long long*>(p.arena + pl.dst_base);
+  unsigned long long* dH = dB + W * ds;
+  unsigned int* dM = reinterpret_cast<unsigned int*>(dH + ds);
+  const unsigned int t = pl.t, L = p.L;
+  const unsigned long long s = pl.s;
+  // level t+1 is stored in the single-level form (t+1 < L' holds for a fused step)
+  const bool close2_ok = t + 2 <= L, store2 = ds != 0, next_ok = t + 3 < L;
+  const unsigned long long gam1 = (unsigned long long)(t + 1) * kGamma, gam2 = (unsigned long long)(t + 2) * kGamma;
+  unsigned long long nx = 0, ncyc1 = 0, ncyc2 = 0, hacc = 0;
+  const unsigned long long T = (unsigned long long)gridDim.x * blockDim.x;
+  const unsigned long long gwarp = ((unsigned long long)wid * gridDim.x + blockIdx.x) * 32ull;
+
+  auto scan = [&](unsigned int cnt, unsigned int& excl, unsigned int& total) {
+    unsigned int incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned int y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= (unsigned)o) incl += y;
+    }
+    excl = incl - cnt;
+    total = __shfl_sync(0xffffffffu, incl, 31);
+  };
+
+  // ---- level t+2: list the staged children's masks (closings or stored children) and
+  // work the entries off, CL at a time
+  auto work2 = [&](const unsigned long long* mk, bool children) {
+    unsigned int cnt = 0;
+#pragma unroll
+    for (int j = 0; j < P2; ++j)
+#pragma unroll
+      for (int k = 0; k < W; ++k) cnt += __popcll(mk[(j * 32 + lane) * W + k]);
+    unsigned int excl, total;
+    scan(cnt, excl, total);
+    for (unsigned int c0 = 0; c0 < total; c0 += CL2) {
+      if (cnt && excl < c0 + CL2 && excl + cnt > c0) {
+        unsigned int idx = excl;
+#pragma unroll
+        for (int j = 0; j < P2; ++j)
+#pragma unroll
+          for (int k = 0; k < W; ++k) {
+            unsigned long long b = mk[(j * 32 + lane) * W + k];
+            while (b) {
+              const unsigned int w = 64u * k + __ffsll((long long)b) - 1;
+              b &= b - 1;
+              if (idx >= c0 && idx < c0 + CL2) sl2[idx - c0] = (unsigned int)(j * 32 + lane) << 8 | w;
+              ++idx;
+            }
+          }
+      }
+      __syncwarp();
+      const unsigned int n = min(CL2, total - c0);
+      if (children) {
+        unsigned long long base = 0;
+        if (lane == 0) base = atomicAdd(&p.ctl->cnt[s % 3], (unsigned long long)n);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        for (unsigned int i = lane; i < n; i += 32) {
+          const unsigned int e = sl2[i], c = e >> 8, w = e & 0xFFu;
+          const unsigned long long slot = base + i;
+          if (slot < ds) {
+            const unsigned int v1 = sv12[c];
+#pragma unroll
+            for (int q = 0; q < W; ++q) {
+              const unsigned long long nb = snb2[c * W + q];
+              dB[q * ds + slot] = nb;
+              if (next_ok)
+                nx += __popcll(adj[(unsigned long long)w * W + q] & ~nb & ~adj[(unsigned long long)v1 * W + q]);
+            }
+            dH[slot] = sh2[c] + rtab[w];
+            dM[slot] = v1 | (w << 16);
+          } else {
+            set_err(p.ctl, kDevBounds, 4);
+          }
+        }
+      } else {
+        for (unsigned int i = lane; i < n; i += 32) {
+          const unsigned int e = sl2[i], c = e >> 8, w = e & 0xFFu;
+          ++ncyc2;
+          hacc += mix64(sh2[c] + rtab[w] + gam2);
+        }
+      }
+      __syncwarp();
+    }
+  };
+
+  // ---- level t+1: the candidates listed in sl[0, n), P2*32 at a time
+  auto expand_children = [&](unsigned int n) {
+    __syncwarp();
+    for (unsigned int r0 = 0; r0 < n; r0 += P2 * 32) {
+#pragma unroll
+      for (int j = 0; j < P2; ++j) {
+        const unsigned int slot = j * 32 + lane, i = r0 + slot;
+        unsigned long long mc[W], mg[W];
+#pragma unroll
+        for (int k = 0; k < W; ++k) mc[k] = mg[k] = 0ull;
+        if (i < n) {
+          const unsigned int e = sl[i], pj = e >> 8, v = e & 0xFFu;
+          const unsigned int v1 = sv1[pj];
+          const unsigned long long hv = sh[pj] + rtab[v];
+          if ((adj[(unsigned long long)v1 * W + (v >> 6)] >> (v & 63u)) & 1ull) {
+            ++ncyc1;
+            hacc += mix64(hv + gam1);
+          } else {
+#pragma unroll
+            for (int k = 0; k < W; ++k) {
+              const unsigned long long nb1 = snb[pj * W + k];  // the child's blocked set
+              const unsigned long long av = adj[(unsigned long long)v * W + k];
+              const unsigned long long a1 = adj[(unsigned long long)v1 * W + k];
+              const unsigned long long cand = av & ~nb1;
+              mc[k] = close2_ok ? (cand & a1) : 0ull;
+              mg[k] = store2 ? (cand & ~a1) : 0ull;
+              snb2[slot * W + k] = nb1 | av;
+            }
+            sh2[slot] = hv;
+            sv12[slot] = v1;
+          }
+        }
+#pragma unroll
+        for (int k = 0; k < W; ++k) {
+          scl2[slot * W + k] = mc[k];
+          sch2[slot * W + k] = mg[k];
+        }
+      }
+      __syncwarp();
+      work2(scl2, false);
+      if (store2) work2(sch2, true);
+    }
+  };
+
+  // ---- level t: load, stage, list every candidate (closing or child)
+  unsigned long long m[P][W];
+  auto list_and_work = [&]() {
+    unsigned int cnt = 0;
+#pragma unroll
+    for (int j = 0; j < P; ++j)
+#pragma unroll
+      for (int k = 0; k < W; ++k) cnt += __popcll(m[j][k]);
+    unsigned int excl, total;
+    scan(cnt, excl, total);
+    for (unsigned int c0 = 0; c0 < total; c0 += CL) {
+      if (cnt && excl < c0 + CL && excl + cnt > c0) {
+        unsigned int idx = excl;
+#pragma unroll
+        for (int j = 0; j < P; ++j)
+#pragma unroll
+          for (int k = 0; k < W; ++k) {
+            unsigned long long b = m[j][k];
+            while (b) {
+              const unsigned int v = 64u * k + __ffsll((long long)b) - 1;
+              b &= b - 1;
+              if (idx >= c0 && idx < c0 + CL) sl[idx - c0] = (unsigned int)(j * 32 + lane) << 8 | v;
+              ++idx;
+            }
+          }
+      }
+      expand_children(min(CL, total - c0));
+    }
+  };
+
+  const unsigned int pf = p.pf >= 1 && p.pf <= (unsigned)P ? p.pf : (unsigned)P;
+  for (unsigned long long wb = pl.begin + gwarp; wb < pl.end; wb += pf * T) {
+    const unsigned long long t0 = wb + lane;
+#pragma unroll
+    for (int j = 0; j < P; ++j) {
+      const unsigned long long i = t0 + (unsigned long long)j * T;
+      const bool valid = (unsigned)j < pf && i < pl.end;
+      unsigned long long B[W];
+#pragma unroll
+      for (int k = 0; k < W; ++k) B[k] = valid ? ldcg64(sB + k * ss + i) : ~0ull;
+      const unsigned long long H = valid ? ldcg64(sH + i) : 0ull;
+      const unsigned int M = valid ? ldcg32(sM + i) : 0u;
+      const unsigned int v1 = M & 0xFFFFu, vt = M >> 16;
+      const unsigned int pj = j * 32 + lane;
+#pragma unroll
+      for (int k = 0; k < W; ++k) {
+        const unsigned long long at = adj[(unsigned long long)vt * W + k];
+        m[j][k] = at & ~B[k];  // candidates: closings and children of t+1 vertices
+        snb[pj * W + k] = B[k] | at;
+      }
+      sh[pj] = H;
+      sv1[pj] = v1;
+    }
+    list_and_work();
+  }
+  // hist[t+1] and hist[t+2]: two block sums
+  block_sum3_u64(nx, ncyc1, hacc, s_red);
+  __syncthreads();
+  unsigned long long z0 = 0, z1 = 0;
+  block_sum3_u64(ncyc2, z0, z1, s_red);
+  if (tid == 0) {
+    if (nx) atomicAdd(&p.ctl->nxt[s % 3], nx);
+    if (ncyc1) atomicAdd(&p.hist[t + 1], ncyc1);
+    if (ncyc2) atomicAdd(&p.hist[t + 2], ncyc2);
     if (hacc) atomicAdd(p.hash, hacc);
   }
 }
@@ -1459,6 +1749,7 @@ __global__ void __launch_bounds__(NT, NT >= 1024 ? 1 : KindTraits<K>::minB) engi
       // staging memory)
       if constexpr (NT >= 1024) process_bitset<K>(p, pl, adj, rtab, s_warp, s_red, &s_base);
       else if constexpr (KindTraits<K>::multi) process_multi_flat<NT>(p, pl, adj, rtab);
+      else if (pl.fuse) process_bitset_fused<K, NT>(p, pl, adj, rtab, s_red);
       else process_bitset_flat<K, NT>(p, pl, adj, rtab, s_red);
     }
     if (blockIdx.x == 0 && tid == 0) {
@@ -1479,7 +1770,7 @@ __global__ void __launch_bounds__(NT, NT >= 1024 ? 1 : KindTraits<K>::minB) engi
       if (err != 0) st.depth = 0;  // every block reads the same word: all stop here
       if (blockIdx.x == 0 && p.step_ts && s < p.step_ts_cap) {
         p.step_ts[s] = globaltimer();
-        if (p.step_rec) p.step_rec[s] = st.chunk;
+        if (p.step_rec) p.step_rec[s] = st.expanded;
       }
     }
     ++s;

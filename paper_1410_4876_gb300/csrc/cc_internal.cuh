@@ -150,7 +150,7 @@ struct EngineParams {
   const unsigned long long* nsig;  // CSR: neighbour signature of each vertex, 2 words [n]
   unsigned long long handover;     // cluster phase: stop before expanding more paths than this
   unsigned int pf;                 // bitset / batch: paths per thread per round (1..P of the kind)
-  unsigned int pad2_;
+  unsigned int fuse_ok;            // one graph, bitset, persistent grid: two-level steps allowed
 };
 
 #ifdef __CUDACC__

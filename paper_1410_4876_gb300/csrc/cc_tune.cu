@@ -6,7 +6,8 @@
 //   1. adjacency form: bitset or CSR (single graphs with n <= 256)
 //   2. launch shape: threads per block x persistent blocks per SM
 //   3. paths per thread per round (bitset and batch expansion)
-//   4. cluster phase: off, or the largest level it expands (bitset single graphs)
+//   4. cluster phase: off, or the largest level it expands; two-level steps on or off
+//      (bitset single graphs)
 // Every candidate's histogram and hash must equal those of the configuration the context
 // had on entry, so a tuning run is also a consistency check of the launch variants.
 // Results are cached per (device name, graph class) in a JSON-lines file.
@@ -145,12 +146,17 @@ cc_status search(cc_options base, bool try_csr, bool single, Run&& run, IsBitset
       if ((s = consider(o))) return s;
     }
   }
-  // 4. cluster phase
+  // 4. cluster phase and two-level steps
   if (single && bitset(best)) {
     const cc_options start = best;
     {
       cc_options o = start;
       o.flags |= CC_FLAG_NO_CLUSTER_PHASE;
+      if ((s = consider(o))) return s;
+    }
+    {
+      cc_options o = start;
+      o.flags ^= CC_FLAG_NO_FUSE;
       if ((s = consider(o))) return s;
     }
     for (unsigned int sp : {8192u, 131072u}) {

@@ -296,8 +296,9 @@ def test_cluster_phase_equals_grid_only(cc):
     # switching that phase off must not change any result
     graphs = [I.grid(6, 6), I.grid(8, 8), I.gnp(60, 0.15, 7), I.wheel(100), I.gnp(100, 2.4 / 100, 100),
               I.complete_bipartite(8, 8)] + _small_graphs(40, 606)
-    with cc.Context(frontier_bytes=2 << 30) as a, \
-            cc.Context(frontier_bytes=2 << 30, flags=cc.CC_FLAG_NO_CLUSTER_PHASE) as b:
+    # (one level per step on both sides, so the step counts compare)
+    with cc.Context(frontier_bytes=2 << 30, flags=cc.CC_FLAG_NO_FUSE) as a, \
+            cc.Context(frontier_bytes=2 << 30, flags=cc.CC_FLAG_NO_CLUSTER_PHASE | cc.CC_FLAG_NO_FUSE) as b:
         for g in graphs:
             ra, rb = a.enumerate(g), b.enumerate(g)
             assert ra.hist.tolist() == rb.hist.tolist() and ra.hash == rb.hash
@@ -309,10 +310,43 @@ def test_cluster_phase_equals_grid_only(cc):
 
 def test_trace_matches_level_counts(cc, ctx):
     g = I.grid(7, 7)
-    r = ctx.enumerate(g)
-    t_ns, expanded = cc.cc_get_trace(ctx.handle)
+    with cc.Context(frontier_bytes=4 << 30, flags=cc.CC_FLAG_NO_FUSE) as c1:
+        r = c1.enumerate(g)
+        t_ns, expanded = cc.cc_get_trace(c1.handle)
     assert len(expanded) == r.info.steps
-    # without spilling every step expands one whole level: the trace lists |T_3|..|T_{L'-1}|
+    # without spilling or two-level steps every step expands one whole level: the trace
+    # lists |T_3|..|T_{L'-1}|
     nz = [int(x) for x in r.tcount if x]
     assert [int(x) for x in expanded] == nz
     assert (np.diff(t_ns.astype(np.int64)) >= 0).all()
+    # with two-level steps a step expands one level or two consecutive ones
+    r2 = ctx.enumerate(g)
+    _, expanded2 = cc.cc_get_trace(ctx.handle)
+    assert r2.tcount.tolist() == r.tcount.tolist() and r2.info.steps < r.info.steps
+    i = 0
+    for e in (int(x) for x in expanded2):
+        if e == nz[i]:
+            i += 1
+        else:
+            assert e == nz[i] + nz[i + 1]
+            i += 2
+    assert i == len(nz)
+
+
+def test_two_level_steps_equal_single_levels(cc):
+    # expanding a level together with its children (storing only the grandchildren) must
+    # not change any result, for every bitset width and with length bounds that end a
+    # two-level step on the last level
+    graphs = [I.grid(6, 6), I.grid(8, 8), I.gnp(60, 0.15, 7), I.wheel(100), I.gnp(100, 2.4 / 100, 100),
+              I.gnp(200, 1.9 / 200, 200), I.complete_bipartite(8, 8)] + _small_graphs(40, 909)
+    with cc.Context(frontier_bytes=2 << 30) as a, \
+            cc.Context(frontier_bytes=2 << 30, flags=cc.CC_FLAG_NO_FUSE) as b:
+        for g in graphs:
+            for L in (0, 5, 6, 9):
+                ra, rb = a.enumerate(g, max_len=L), b.enumerate(g, max_len=L)
+                assert ra.hist.tolist() == rb.hist.tolist() and ra.hash == rb.hash, (g.name, L)
+                assert ra.tcount.tolist() == rb.tcount.tolist(), (g.name, L)
+                assert ra.info.steps <= rb.info.steps
+        for g in graphs[7:]:
+            _same(a.enumerate(g), oracle.enumerate_cycles(g))
+        _same(a.enumerate(graphs[4], max_len=9), oracle.enumerate_cycles(graphs[4], max_len=9))
