@@ -72,6 +72,14 @@ def test_grid6x10_table1(ctx):
     assert r.total == 800139  # Table 1
 
 
+def test_wheel_with_hub_closed_form(ctx):
+    # W_k: k triangles and the rim; n = 1501 with a hub of degree 1500, CSR path with
+    # paths of up to 1500 vertices
+    k = 1500
+    r = ctx.enumerate(I.wheel(k))
+    assert r.total == k + 1 and int(r.hist[3]) == k and int(r.hist[k]) == 1
+
+
 @pytest.mark.parametrize("k,l,total", [(7, 10, 8136453), (8, 10, 71535910)])
 def test_large_grids_table1(ctx, k, l, total):
     # the two largest synthetic rows of Table 1 (no triangles in a grid, so the total is
