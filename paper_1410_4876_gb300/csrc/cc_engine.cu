@@ -12,6 +12,8 @@
 // or bounded child count fits the free arena, else the largest chunk that fits; that
 // chunk's subtree then runs depth-first), expand those paths with one thread per path,
 // compact the children with a block scan and one atomic per tile, accumulate cycles.
+#include <cooperative_groups.h>
+
 #include "cc_internal.cuh"
 
 namespace cc {
@@ -122,8 +124,8 @@ __device__ bool plan_step(const EngineParams& p, LocalState& st, StepPlan& pl) {
       const unsigned long long need2 = (t + 2 < p.L) ? f.next * p.maxch : 0ull;
       const unsigned long long rb2 = record_bytes<K>(t + 2);
       const unsigned long long freeb = st.top - st.bot;
-      const unsigned long long maxcap2 = freeb > 1024 ? ((freeb - 1024) / rb2) & ~7ull : 0ull;
-      if (need2 <= maxcap2) {
+      // (a multiply-compare: the planner runs on one thread per block every step)
+      if (freeb > 1024 && (round_up(need2, 8) + 8) * rb2 <= freeb - 1024) {
         st.fused = 1;
         pl.fuse = 1;
         if (need2 > 0) {
@@ -148,7 +150,10 @@ __device__ bool plan_step(const EngineParams& p, LocalState& st, StepPlan& pl) {
   if (cap > 0) {
     const unsigned long long rb = record_bytes<K>(t + 1);
     const unsigned long long freeb = st.top - st.bot;
-    const unsigned long long maxcap = freeb > 1024 ? ((freeb - 1024) / rb) & ~7ull : 0ull;
+    // the division is only needed when the level does not fit (the common case is a
+    // multiply-compare)
+    const bool fits = freeb > 1024 && (round_up(cap, 8) + 8) * rb <= freeb - 1024;
+    const unsigned long long maxcap = fits ? cap : (freeb > 1024 ? ((freeb - 1024) / rb) & ~7ull : 0ull);
     if (cap > maxcap) {
       // Spill: this chunk's subtree runs depth-first before the rest of the frame, and
       // each deeper stored level of that subtree needs room too, so the chunk's children
@@ -210,6 +215,10 @@ __device__ void commit_step(const EngineParams& p, LocalState& st, unsigned long
   }
   if (st.has_child && c > 0) {
     Frame g = st.child;
+    if (c > g.stride) {  // more children than the planned bound (the writes past it were skipped)
+      set_err(p.ctl, kDevCapacity, (int)t);
+      c = g.stride;
+    }
     g.count = c;
     g.cursor = 0;
     g.next = nx;  // exact (bitset, batch) or an upper bound (CSR)
@@ -275,7 +284,8 @@ template <Kind K>
 __device__ __forceinline__ void process_bitset(const EngineParams& p, const StepPlan& pl,
                                                const unsigned long long* adj, const unsigned long long* rtab,
                                                unsigned int* s_warp, unsigned long long* s_red,
-                                               unsigned long long* s_base) {
+                                               unsigned long long* s_base, unsigned long long* cntp,
+                                               unsigned long long* nxtp) {
   constexpr int W = KindTraits<K>::W;
   constexpr int P = KindTraits<K>::P;
   constexpr bool MULTI = KindTraits<K>::multi;
@@ -400,7 +410,7 @@ __device__ __forceinline__ void process_bitset(const EngineParams& p, const Step
     }
     if (store) {
       // children slots: warp scan and one atomic per warp (no block barrier)
-      const unsigned long long off = warp_slots(nch, &p.ctl->cnt[s % 3]);
+      const unsigned long long off = warp_slots(nch, &cntp[s % 3]);
       if (__any_sync(0xffffffffu, nch != 0)) {
         unsigned long long slot = off;
 #pragma unroll
@@ -463,7 +473,7 @@ __device__ __forceinline__ void process_bitset(const EngineParams& p, const Step
   if constexpr (MULTI) run.flush(p, s);
   block_sum3_u64(nx, ncyc, hacc, s_red);
   if (tid == 0) {
-    if (nx) atomicAdd(&p.ctl->nxt[s % 3], nx);
+    if (nx) atomicAdd(&nxtp[s % 3], nx);
     if (!MULTI && ncyc) atomicAdd(&p.hist[t + 1], ncyc);
     if (!MULTI && hacc) atomicAdd(p.hash, hacc);
   }
@@ -1690,6 +1700,20 @@ __global__ void __launch_bounds__(NT, NT >= 1024 ? 1 : KindTraits<K>::minB) engi
     }
   }
 
+  // Step counters (child slots, next-level size): global for the persistent grid; in the
+  // cluster phase they live in CTA 0's shared memory and every CTA reaches them as
+  // distributed shared memory (no L2 round trip for the slot atomics and the reads)
+  __shared__ unsigned long long s_ctr[6];
+  unsigned long long* cntp = p.ctl->cnt;
+  unsigned long long* nxtp = p.ctl->nxt;
+  if constexpr (NT >= 1024) {
+    if (tid < 6) s_ctr[tid] = 0ull;
+    unsigned long long* c0 = cooperative_groups::this_cluster().map_shared_rank(s_ctr, 0);
+    cntp = c0;
+    nxtp = c0 + 3;
+    cluster_barrier();  // the zeros are visible before any CTA adds to them
+  }
+
   if (tid == 0) {
     Control* c = p.ctl;
     if (p.fresh) {
@@ -1747,14 +1771,14 @@ __global__ void __launch_bounds__(NT, NT >= 1024 ? 1 : KindTraits<K>::minB) engi
       // the flattened form for the persistent grid (the small cluster phase keeps the
       // per-lane form: its levels are small and its 32 warps per block would need 4x the
       // staging memory)
-      if constexpr (NT >= 1024) process_bitset<K>(p, pl, adj, rtab, s_warp, s_red, &s_base);
+      if constexpr (NT >= 1024) process_bitset<K>(p, pl, adj, rtab, s_warp, s_red, &s_base, cntp, nxtp);
       else if constexpr (KindTraits<K>::multi) process_multi_flat<NT>(p, pl, adj, rtab);
       else if (pl.fuse) process_bitset_fused<K, NT>(p, pl, adj, rtab, s_red);
       else process_bitset_flat<K, NT>(p, pl, adj, rtab, s_red);
     }
     if (blockIdx.x == 0 && tid == 0) {
-      p.ctl->cnt[(s + 1) % 3] = 0;
-      p.ctl->nxt[(s + 1) % 3] = 0;
+      cntp[(s + 1) % 3] = 0;
+      nxtp[(s + 1) % 3] = 0;
     }
     if (p.cluster) {
       cluster_barrier();
@@ -1763,9 +1787,17 @@ __global__ void __launch_bounds__(NT, NT >= 1024 ? 1 : KindTraits<K>::minB) engi
     }
     if (tid == 0) {
       // the step's counters and the error word, in one round trip
-      const unsigned long long c = ld_relaxed_u64(&p.ctl->cnt[s % 3]);
-      const unsigned long long nx = ld_relaxed_u64(&p.ctl->nxt[s % 3]);
-      const int err = ld_relaxed_i32(&p.ctl->err);
+      unsigned long long c, nx;
+      if constexpr (NT >= 1024) {
+        c = *reinterpret_cast<volatile unsigned long long*>(&cntp[s % 3]);
+        nx = *reinterpret_cast<volatile unsigned long long*>(&nxtp[s % 3]);
+      } else {
+        c = ld_relaxed_u64(&p.ctl->cnt[s % 3]);
+        nx = ld_relaxed_u64(&p.ctl->nxt[s % 3]);
+      }
+      // (the cluster phase has no barrier that can time out and a child count is clamped to
+      // its frame, so it leaves the error word to the grid phase and to the host)
+      const int err = NT >= 1024 ? 0 : ld_relaxed_i32(&p.ctl->err);
       commit_step<K>(p, st, c, nx, blockIdx.x == 0);
       if (err != 0) st.depth = 0;  // every block reads the same word: all stop here
       if (blockIdx.x == 0 && p.step_ts && s < p.step_ts_cap) {
@@ -1776,6 +1808,8 @@ __global__ void __launch_bounds__(NT, NT >= 1024 ? 1 : KindTraits<K>::minB) engi
     ++s;
     ++steps_here;
   }
+  // cluster phase: CTA 0's shared memory (the counters) must outlive every CTA's reads
+  if constexpr (NT >= 1024) cluster_barrier();
   if (blockIdx.x == 0 && tid == 0) {
     Control* c = p.ctl;
     c->depth = st.depth;
