@@ -899,7 +899,7 @@ __device__ __forceinline__ void process_multi_flat(const EngineParams& p, const 
   const unsigned int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   unsigned long long* snb = fs.nb[wid];
   unsigned long long* sh = fs.h[wid];
-  unsigned int* smeta = fs.v1[wid];  // v1 | t << 6 | g << 12
+  unsigned int* smeta = fs.v1[wid];  // v1 | t << 6 | g << 12 | (t + 2 < L'_g) << 31
   unsigned int* sl = fs.list[wid];
   const unsigned long long ss = pl.src_stride, ds = pl.dst_stride;
   const unsigned long long* sB = reinterpret_cast<const unsigned long long*>(p.arena + pl.src_base);
@@ -922,14 +922,14 @@ __device__ __forceinline__ void process_multi_flat(const EngineParams& p, const 
     base = __shfl_sync(0xffffffffu, base, 0);
     for (unsigned int i = lane; i < n; i += 32) {
       const unsigned int e = sl[i], pj = e >> 8, v = e & 0xFFu;
-      const unsigned int meta = smeta[pj], v1 = meta & 63u, tt = (meta >> 6) & 63u, g = meta >> 12;
+      const unsigned int meta = smeta[pj], v1 = meta & 63u, tt = (meta >> 6) & 63u, g = (meta >> 12) & 0x7FFFFu;
       const unsigned long long go = (unsigned long long)g * 64ull, slot = base + i;
       if (slot < ds) {
         const unsigned long long nb = snb[pj];
         dB[slot] = nb;
         dH[slot] = sh[pj] + __ldg(rtab + go + v);
         dM[slot] = v1 | (v << 6) | ((tt + 1) << 12) | (g << 18);
-        if (tt + 2 < p.Lg[g]) nx += __popcll(__ldg(adj + go + v) & ~nb & ~__ldg(adj + go + v1));
+        if (meta >> 31) nx += __popcll(__ldg(adj + go + v) & ~nb & ~__ldg(adj + go + v1));
       } else {
         set_err(p.ctl, kDevBounds, 1);
       }
@@ -945,14 +945,18 @@ __device__ __forceinline__ void process_multi_flat(const EngineParams& p, const 
       if (i < n) {
         const unsigned int e = sl[i], pj = e >> 8, v = e & 0xFFu;
         const unsigned int meta = smeta[pj], tt = (meta >> 6) & 63u;
-        g = meta >> 12;
+        g = (meta >> 12) & 0x7FFFFu;
         h = mix64(sh[pj] + __ldg(rtab + (unsigned long long)g * 64ull + v) + (unsigned long long)(tt + 1) * kGamma);
       }
-      // one atomic per distinct slot among the lanes
-      const unsigned int grp = __match_any_sync(0xffffffffu, g);
-      unsigned long long sum = 0;
-      for (unsigned int m = grp; m; m &= m - 1) sum += __shfl_sync(grp, h, __ffs(m) - 1);
-      if (g != 0xFFFFFFFFu && lane == (unsigned)(__ffs(grp) - 1)) atomicAdd(&p.hash[g], sum);
+      // a frontier keeps each graph's records together: usually every active lane of a
+      // round closes cycles of one slot (one warp sum, one atomic); otherwise per lane
+      const unsigned int g0 = __shfl_sync(0xffffffffu, g, 0);  // lane 0 is active (n > r0)
+      if (__all_sync(0xffffffffu, g == g0 || i >= n)) {
+        const unsigned long long sum = warp_sum_u64(h);
+        if (lane == 0) atomicAdd(&p.hash[g0], sum);
+      } else if (i < n) {
+        atomicAdd(&p.hash[g], h);
+      }
     }
     __syncwarp();
   };
@@ -1012,7 +1016,7 @@ __device__ __forceinline__ void process_multi_flat(const EngineParams& p, const 
       const unsigned int pj = j * 32 + lane;
       snb[pj] = B | at;
       sh[pj] = H;
-      smeta[pj] = v1 | (tt << 6) | (g << 12);
+      smeta[pj] = v1 | (tt << 6) | (g << 12) | ((tt + 2 < Lr) ? 0x80000000u : 0u);
       key[j] = valid ? (g << 6 | tt) : 0xFFFFFFFFu;
       nc[j] = __popcll(m[j]);
       nk[j] = __popcll(ch[j]);
