@@ -461,10 +461,18 @@ def run_serve(args):
 
 
 def _engine_fingerprint() -> str:
+    """Hash of the engine's code (cc_engine.cu + cc_internal.cuh without comments and
+    whitespace), so that a committed ncu capture is used only for the code it measured."""
     import hashlib
+    import re
     csrc = os.path.join(ROOT, "paper_1410_4876_gb300", "csrc")
-    data = open(os.path.join(csrc, "cc_engine.cu"), "rb").read() + open(os.path.join(csrc, "cc_internal.cuh"), "rb").read()
-    return hashlib.sha256(data).hexdigest()[:16]
+    text = ""
+    for f in ("cc_engine.cu", "cc_internal.cuh"):
+        src = open(os.path.join(csrc, f)).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", "", src)
+        text += re.sub(r"\s+", "", src)
+    return hashlib.sha256(text.encode()).hexdigest()[:16]
 
 
 def _ncu_traffic(workload: str):

@@ -10,8 +10,14 @@
 //
 // Per step: take the top frame, choose how much of it to expand (all of it if the exact
 // or bounded child count fits the free arena, else the largest chunk that fits; that
-// chunk's subtree then runs depth-first), expand those paths with one thread per path,
-// compact the children with a block scan and one atomic per tile, accumulate cycles.
+// chunk's subtree then runs depth-first; a bitset level whose children are known exactly
+// and grow slowly is expanded together with them), expand those paths, list their
+// children and closings as (path, vertex) entries worked off one per lane, give each
+// warp's child list its slots with one atomic, accumulate cycles.
+//
+// Expansion forms: process_bitset_flat / process_bitset_fused (one graph, bitset
+// adjacency), process_multi_flat (batch and serving), process_bitset (the small-level
+// cluster phase), process_csr_coop / process_csr_last / process_csr_long (CSR adjacency).
 #include <cooperative_groups.h>
 
 #include "cc_internal.cuh"
