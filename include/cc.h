@@ -199,17 +199,20 @@ cc_status cc_enumerate(cc_graph* g, uint32_t max_len, uint64_t* out_hist, uint64
                        uint64_t* out_tcount, cc_cycles* out_cycles, cc_run_info* out_info);
 
 /*
- * CUDA graphs: without out_cycles and without CC_FLAG_NO_GRAPH, the second cc_enumerate of
- * a graph with the same max_len and launch configuration captures its device work (result
- * resets, labelling, seeding, the expansion launches and the result copies) into a CUDA
- * graph kept with the cc_graph, and that call and later ones with the same configuration
- * replay it with one launch (cc_run_info.replayed).  If capture is not possible the
- * kernels are launched directly; the results are the same either way.
+ * CUDA graphs (the paper relaunches its kernels from the host, Algorithm 4; here a whole
+ * call is one replayable unit).  Without out_cycles and without CC_FLAG_NO_GRAPH, the
+ * second cc_enumerate of a graph with the same max_len and launch configuration captures
+ * its device work (result resets, labelling, seeding, the expansion launches and the
+ * result copies) into a CUDA graph kept with the cc_graph, and that call and later ones
+ * with the same configuration replay it with one launch (cc_run_info.replayed).  If
+ * capture is not possible the kernels are launched directly; the results are the same
+ * either way.
  */
 
 /*
- * Autotuner.  Times candidate launch configurations of cc_enumerate on graph g (all
- * lengths up to max_len) and returns the fastest:
+ * Autotuner (the paper sets its work sizes by hand, globalSize = |SM| x MaxSMSize in
+ * Section 4.4; here they are measured).  Times candidate launch configurations of
+ * cc_enumerate on graph g (all lengths up to max_len) and returns the fastest:
  *   bitset or CSR adjacency (when n <= 256), threads_per_block x blocks_per_sm,
  *   paths_per_thread (bitset), the cluster phase (off, or small_phase_paths) and
  *   two-level steps (CC_FLAG_NO_FUSE).
