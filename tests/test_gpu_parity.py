@@ -104,6 +104,22 @@ def test_edge_cases(ctx):
         _same(r, ref)
 
 
+def test_largest_n(cc, ctx):
+    # n at the CSR limit (32768): the labelling's longest sequential loop, and a graph too
+    # large for the shared-memory staging (rows, ids and signatures are read from global
+    # memory); against the oracle with a length bound
+    lim = cc.cc_get_limits()
+    g = I.gnm(lim.max_n_csr, 40000, 1)
+    _same(ctx.enumerate(g, max_len=8), oracle.enumerate_cycles(g, max_len=8))
+    # one more vertex is refused on the host
+    big = I.gnm(lim.max_n_csr + 1, 10, 1)
+    s, _ = cc.cc_graph_load(ctx.handle, big.n, big.row_ptr, big.col)
+    assert s == cc.CC_ERR_UNSUPPORTED
+    # a long cycle: one chordless cycle of 4096 vertices, paths of up to 4095 vertices
+    r = ctx.enumerate(I.cycle(4096))
+    assert r.total == 1 and int(r.hist[4096]) == 1
+
+
 def test_invalid_graphs(cc, ctx):
     bad = [
         (3, [0, 1, 1, 1], [1]),               # 0 -> 1 without 1 -> 0
