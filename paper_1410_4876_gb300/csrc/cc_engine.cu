@@ -70,7 +70,8 @@ struct KindTraits {
   // paths per thread per tile, and the minimum resident 256-thread blocks per SM the
   // register allocation must allow (4 blocks = 64 registers per thread, 3 = 85, 2 = 128)
   static constexpr int P = K == Kind::Bitset4 ? 1 : (K == Kind::Bitset1 ? 3 : 2);
-  static constexpr int minB = (K == Kind::Csr || K == Kind::Csr32) ? 2 : ((K == Kind::Multi || K == Kind::Csr16) ? 3 : 4);
+  static constexpr int minB =
+      (K == Kind::Csr || K == Kind::Csr32) ? 2 : ((K == Kind::Multi || K == Kind::Csr16 || K == Kind::Bitset1) ? 3 : 4);
   // paths per thread per round of the flattened single-graph form (one slot atomic per
   // warp per round)
   static constexpr int PF = K == Kind::Bitset1 ? 3 : (K == Kind::Bitset2 ? 2 : 1);
@@ -90,6 +91,11 @@ __device__ __forceinline__ unsigned long long record_bytes(unsigned int t_child)
 }
 
 // ------------------------------------------------------------------ control (thread 0)
+
+// In sparse graphs (at most this many children per path) two-level steps are taken
+// however fast the levels grow: the per-step floor (barrier and counter round trips) and
+// the frontier traffic of the skipped level outweigh the staging cost.
+constexpr unsigned int kFuseSparseMaxch = 4;
 
 template <Kind K>
 __device__ bool plan_step(const EngineParams& p, LocalState& st, StepPlan& pl) {
@@ -122,11 +128,12 @@ __device__ bool plan_step(const EngineParams& p, LocalState& st, StepPlan& pl) {
     // is expanded, its children are expanded in the same step without being stored, and
     // only the grandchildren (level t+2) are stored.  Their count is bounded by
     // children * maxch; the step is taken only when that bound fits the free arena
-    // (otherwise the level runs alone and may be split into depth-first chunks), and
-    // only while the frontier grows by at most 1.3x per level (measured: steps of
-    // fast-growing levels are quicker one level at a time).
+    // (otherwise the level runs alone and may be split into depth-first chunks), and,
+    // unless the graph is sparse, only while the frontier grows by at most 1.3x per level
+    // (measured: in denser graphs, steps of fast-growing levels are quicker one level at a
+    // time).
     if (p.fuse_ok && !p.cluster && t + 1 < p.L && f.cursor == 0 && f.next != kNoNext && f.next > 0 &&
-        f.next * 10ull <= f.count * 13ull) {
+        (f.next * 10ull <= f.count * 13ull || p.maxch <= kFuseSparseMaxch)) {
       const unsigned long long need2 = (t + 2 < p.L) ? f.next * p.maxch : 0ull;
       const unsigned long long rb2 = record_bytes<K>(t + 2);
       const unsigned long long freeb = st.top - st.bot;
@@ -487,12 +494,12 @@ __device__ __forceinline__ void process_bitset(const EngineParams& p, const Step
 
 // Single-graph bitset expansion with flattened output.  The per-path part (load B, H, M;
 // cand = Adj(vt) & ~B, close = cand & Adj(v1), child = cand & ~Adj(v1)) is as above, but
-// each path's B | Adj(vt), H and v1 are staged in shared memory and its children and
-// closings are listed as (path, vertex) entries.  The entries are then worked off with
-// one entry per lane: a child list takes its slots with one atomic and lane i writes
-// slot base + i, so each plane is stored contiguously; a closing list adds
-// h(C) = mix(H + r(v) + (t+1) gamma).  This replaces the per-lane loops over a path's
-// children, whose cost was set by the lane with the most children.
+// each path's B | Adj(vt), H and v1 are staged in shared memory and its children are
+// listed as (path, vertex) entries.  The entries are then worked off with one entry per
+// lane: a warp's child list takes its slots with one atomic and lane i writes slot
+// base + i, so each plane is stored contiguously.  This replaces the per-lane loops over
+// a path's children, whose cost was set by the lane with the most children.  Closings
+// (a few per path) add h(C) = mix(H + r(v) + (t+1) gamma) in place, lane by lane.
 template <int W, int P, int NT>
 struct FlatSmem {
   static constexpr unsigned int CL = 64 * P > 256 ? 256 : 64 * P;  // list entries per warp
@@ -537,45 +544,12 @@ __device__ __forceinline__ void process_bitset_flat(const EngineParams& p, const
   const unsigned long long T = (unsigned long long)gridDim.x * blockDim.x;
   const unsigned long long gwarp = ((unsigned long long)wid * gridDim.x + blockIdx.x) * 32ull;
 
-  // children entries [0, n): slots from one atomic, lane i writes slot base + i
-  auto flush_children = [&](unsigned int n) {
-    __syncwarp();
-    unsigned long long base = 0;
-    if (lane == 0) base = atomicAdd(&p.ctl->cnt[s % 3], (unsigned long long)n);
-    base = __shfl_sync(0xffffffffu, base, 0);
-    for (unsigned int i = lane; i < n; i += 32) {
-      const unsigned int e = sl[i], pj = e >> 8, v = e & 0xFFu;
-      const unsigned long long slot = base + i;
-      if (slot < ds) {
-        const unsigned int v1 = sv1[pj];
-#pragma unroll
-        for (int q = 0; q < W; ++q) {
-          const unsigned long long nb = snb[pj * W + q];
-          dB[q * ds + slot] = nb;
-          if (next_ok) nx += __popcll(adj[(unsigned long long)v * W + q] & ~nb & ~adj[(unsigned long long)v1 * W + q]);
-        }
-        dH[slot] = sh[pj] + rtab[v];
-        dM[slot] = v1 | (v << 16);
-      } else {
-        set_err(p.ctl, kDevBounds, 1);
-      }
-    }
-    __syncwarp();
-  };
-  // closing entries [0, n)
-  auto flush_closings = [&](unsigned int n) {
-    __syncwarp();
-    for (unsigned int i = lane; i < n; i += 32) {
-      const unsigned int e = sl[i], pj = e >> 8, v = e & 0xFFu;
-      ++ncyc;
-      hacc += mix64(sh[pj] + rtab[v] + gam);
-    }
-    __syncwarp();
-  };
-  // list the set bits of m[j][k] (j < P, k < W) as entries, in chunks of CL, and work
-  // each chunk off with `work`
-  unsigned long long m[P][W];  // the masks being listed
-  auto list_and_work = [&](bool children) {
+  // list the set bits of m[j][k] (j < P, k < W), the children of the staged paths, as
+  // entries, CL at a time, and write each chunk out with one entry per lane.  The warp's
+  // slots come from one atomic, issued before the listing so that its round trip overlaps
+  // it; lane i writes slot base + c0 + i, so each plane is stored contiguously.
+  unsigned long long m[P][W];
+  auto list_children = [&]() {
     unsigned int cnt = 0;
 #pragma unroll
     for (int j = 0; j < P; ++j)
@@ -588,6 +562,9 @@ __device__ __forceinline__ void process_bitset_flat(const EngineParams& p, const
       if (lane >= (unsigned)o) incl += y;
     }
     const unsigned int excl = incl - cnt, total = __shfl_sync(0xffffffffu, incl, 31);
+    if (total == 0) return;
+    unsigned long long base = 0;
+    if (lane == 0) base = atomicAdd(&p.ctl->cnt[s % 3], (unsigned long long)total);
     for (unsigned int c0 = 0; c0 < total; c0 += CL) {
       if (cnt && excl < c0 + CL && excl + cnt > c0) {
         unsigned int idx = excl;
@@ -604,15 +581,34 @@ __device__ __forceinline__ void process_bitset_flat(const EngineParams& p, const
             }
           }
       }
-      if (children) flush_children(min(CL, total - c0));
-      else flush_closings(min(CL, total - c0));
+      __syncwarp();
+      const unsigned long long b0 = __shfl_sync(0xffffffffu, base, 0) + c0;
+      const unsigned int n = min(CL, total - c0);
+      for (unsigned int i = lane; i < n; i += 32) {
+        const unsigned int e = sl[i], pj = e >> 8, v = e & 0xFFu;
+        const unsigned long long slot = b0 + i;
+        if (slot < ds) {
+          const unsigned int v1 = sv1[pj];
+#pragma unroll
+          for (int q = 0; q < W; ++q) {
+            const unsigned long long nb = snb[pj * W + q];
+            dB[q * ds + slot] = nb;
+            if (next_ok) nx += __popcll(adj[(unsigned long long)v * W + q] & ~nb & ~adj[(unsigned long long)v1 * W + q]);
+          }
+          dH[slot] = sh[pj] + rtab[v];
+          dM[slot] = v1 | (v << 16);
+        } else {
+          set_err(p.ctl, kDevBounds, 1);
+        }
+      }
+      __syncwarp();
     }
   };
 
   const unsigned int pf = p.pf >= 1 && p.pf <= (unsigned)P ? p.pf : (unsigned)P;
   for (unsigned long long wb = pl.begin + gwarp; wb < pl.end; wb += pf * T) {
     const unsigned long long t0 = wb + lane;
-    unsigned long long ch[P][W];
+    unsigned long long cm[P][W];
 #pragma unroll
     for (int j = 0; j < P; ++j) {
       const unsigned long long i = t0 + (unsigned long long)j * T;
@@ -629,21 +625,30 @@ __device__ __forceinline__ void process_bitset_flat(const EngineParams& p, const
         const unsigned long long at = adj[(unsigned long long)vt * W + k];
         const unsigned long long a1 = adj[(unsigned long long)v1 * W + k];
         const unsigned long long cand = at & ~B[k];
-        m[j][k] = close_ok ? (cand & a1) : 0ull;
-        ch[j][k] = store ? (cand & ~a1) : 0ull;
+        m[j][k] = store ? (cand & ~a1) : 0ull;
+        cm[j][k] = close_ok ? (cand & a1) : 0ull;
         snb[pj * W + k] = B[k] | at;
       }
       sh[pj] = H;
       sv1[pj] = v1;
     }
-    list_and_work(false);
-    if (store) {
+    // closings <p, v> (a few per path): hashed in place, lane by lane
 #pragma unroll
-      for (int j = 0; j < P; ++j)
+    for (int j = 0; j < P; ++j)
 #pragma unroll
-        for (int k = 0; k < W; ++k) m[j][k] = ch[j][k];
-      list_and_work(true);
-    }
+      for (int k = 0; k < W; ++k) {
+        unsigned long long cb = cm[j][k];
+        if (cb) {
+          const unsigned long long H = sh[j * 32 + lane];
+          do {
+            const unsigned int v = 64u * k + __ffsll((long long)cb) - 1;
+            cb &= cb - 1;
+            ++ncyc;
+            hacc += mix64(H + rtab[v] + gam);
+          } while (cb);
+        }
+      }
+    if (store) list_children();
   }
   block_sum3_u64(nx, ncyc, hacc, s_red);
   if (tid == 0) {
@@ -654,18 +659,17 @@ __device__ __forceinline__ void process_bitset_flat(const EngineParams& p, const
 }
 
 // Two levels in one step (single graph, bitset).  Level t is expanded as in the flattened
-// form, but every candidate (closing or child) is listed once; the list is worked off P*32
-// entries at a time: a candidate adjacent to v1 closes a cycle of t+1 vertices, any other
-// is a child of level t+1, which is not stored but staged in shared memory with its
-// blocked set B | Adj(vt) | Adj(v), H + r(v) and its closing / child masks.  The staged
-// children (P2 rounds of 32 at a time) are then expanded in the flattened way, and only
-// their children (level t+2) are stored, with their exact child counts summed for the
-// next frame.
+// form, but every candidate (closing or child) is listed once; the list is worked off
+// P2*32 entries at a time: a candidate adjacent to v1 closes a cycle of t+1 vertices, any
+// other is a child of level t+1, which is not stored.  Its own closings (cycles of t+2
+// vertices) are hashed in place, and it is staged in shared memory with its blocked set
+// B | Adj(vt) | Adj(v), H + r(v) and its child mask.  The staged children's children
+// (level t+2) are then listed and stored in the flattened way, with their exact child
+// counts summed for the next frame.
 template <int W, int P, int NT>
 struct FusedSmem {
   unsigned long long nb[NT / 32][P * 32 * W];  // staged children: blocked set of their children
   unsigned long long h[NT / 32][P * 32];       // their H'
-  unsigned long long cl[NT / 32][P * 32 * W];  // closing mask (cycles of t+2 vertices)
   unsigned long long ch[NT / 32][P * 32 * W];  // child mask (stored paths of t+2 vertices)
   unsigned int v1[NT / 32][P * 32];
   unsigned int list[NT / 32][64 * P];  // level t+2 entries: slot << 8 | w
@@ -687,7 +691,6 @@ __device__ __forceinline__ void process_bitset_fused(const EngineParams& p, cons
   unsigned int* sl = fs.list[wid];
   unsigned long long* snb2 = fs2.nb[wid];
   unsigned long long* sh2 = fs2.h[wid];
-  unsigned long long* scl2 = fs2.cl[wid];
   unsigned long long* sch2 = fs2.ch[wid];
   unsigned int* sv12 = fs2.v1[wid];
   unsigned int* sl2 = fs2.list[wid];
@@ -718,16 +721,19 @@ __device__ __forceinline__ void process_bitset_fused(const EngineParams& p, cons
     total = __shfl_sync(0xffffffffu, incl, 31);
   };
 
-  // ---- level t+2: list the staged children's masks (closings or stored children) and
-  // work the entries off, CL at a time
-  auto work2 = [&](const unsigned long long* mk, bool children) {
+  // ---- level t+2: list the staged children's child masks and write the entries out,
+  // CL2 at a time (slots from one atomic per list, issued before the listing)
+  auto list2_children = [&]() {
     unsigned int cnt = 0;
 #pragma unroll
     for (int j = 0; j < P2; ++j)
 #pragma unroll
-      for (int k = 0; k < W; ++k) cnt += __popcll(mk[(j * 32 + lane) * W + k]);
+      for (int k = 0; k < W; ++k) cnt += __popcll(sch2[(j * 32 + lane) * W + k]);
     unsigned int excl, total;
     scan(cnt, excl, total);
+    if (total == 0) return;
+    unsigned long long base = 0;
+    if (lane == 0) base = atomicAdd(&p.ctl->cnt[s % 3], (unsigned long long)total);
     for (unsigned int c0 = 0; c0 < total; c0 += CL2) {
       if (cnt && excl < c0 + CL2 && excl + cnt > c0) {
         unsigned int idx = excl;
@@ -735,7 +741,7 @@ __device__ __forceinline__ void process_bitset_fused(const EngineParams& p, cons
         for (int j = 0; j < P2; ++j)
 #pragma unroll
           for (int k = 0; k < W; ++k) {
-            unsigned long long b = mk[(j * 32 + lane) * W + k];
+            unsigned long long b = sch2[(j * 32 + lane) * W + k];
             while (b) {
               const unsigned int w = 64u * k + __ffsll((long long)b) - 1;
               b &= b - 1;
@@ -745,34 +751,24 @@ __device__ __forceinline__ void process_bitset_fused(const EngineParams& p, cons
           }
       }
       __syncwarp();
+      const unsigned long long b0 = __shfl_sync(0xffffffffu, base, 0) + c0;
       const unsigned int n = min(CL2, total - c0);
-      if (children) {
-        unsigned long long base = 0;
-        if (lane == 0) base = atomicAdd(&p.ctl->cnt[s % 3], (unsigned long long)n);
-        base = __shfl_sync(0xffffffffu, base, 0);
-        for (unsigned int i = lane; i < n; i += 32) {
-          const unsigned int e = sl2[i], c = e >> 8, w = e & 0xFFu;
-          const unsigned long long slot = base + i;
-          if (slot < ds) {
-            const unsigned int v1 = sv12[c];
+      for (unsigned int i = lane; i < n; i += 32) {
+        const unsigned int e = sl2[i], c = e >> 8, w = e & 0xFFu;
+        const unsigned long long slot = b0 + i;
+        if (slot < ds) {
+          const unsigned int v1 = sv12[c];
 #pragma unroll
-            for (int q = 0; q < W; ++q) {
-              const unsigned long long nb = snb2[c * W + q];
-              dB[q * ds + slot] = nb;
-              if (next_ok)
-                nx += __popcll(adj[(unsigned long long)w * W + q] & ~nb & ~adj[(unsigned long long)v1 * W + q]);
-            }
-            dH[slot] = sh2[c] + rtab[w];
-            dM[slot] = v1 | (w << 16);
-          } else {
-            set_err(p.ctl, kDevBounds, 4);
+          for (int q = 0; q < W; ++q) {
+            const unsigned long long nb = snb2[c * W + q];
+            dB[q * ds + slot] = nb;
+            if (next_ok)
+              nx += __popcll(adj[(unsigned long long)w * W + q] & ~nb & ~adj[(unsigned long long)v1 * W + q]);
           }
-        }
-      } else {
-        for (unsigned int i = lane; i < n; i += 32) {
-          const unsigned int e = sl2[i], c = e >> 8, w = e & 0xFFu;
-          ++ncyc2;
-          hacc += mix64(sh2[c] + rtab[w] + gam2);
+          dH[slot] = sh2[c] + rtab[w];
+          dM[slot] = v1 | (w << 16);
+        } else {
+          set_err(p.ctl, kDevBounds, 4);
         }
       }
       __syncwarp();
@@ -786,9 +782,9 @@ __device__ __forceinline__ void process_bitset_fused(const EngineParams& p, cons
 #pragma unroll
       for (int j = 0; j < P2; ++j) {
         const unsigned int slot = j * 32 + lane, i = r0 + slot;
-        unsigned long long mc[W], mg[W];
+        unsigned long long mg[W];
 #pragma unroll
-        for (int k = 0; k < W; ++k) mc[k] = mg[k] = 0ull;
+        for (int k = 0; k < W; ++k) mg[k] = 0ull;
         if (i < n) {
           const unsigned int e = sl[i], pj = e >> 8, v = e & 0xFFu;
           const unsigned int v1 = sv1[pj];
@@ -803,23 +799,26 @@ __device__ __forceinline__ void process_bitset_fused(const EngineParams& p, cons
               const unsigned long long av = adj[(unsigned long long)v * W + k];
               const unsigned long long a1 = adj[(unsigned long long)v1 * W + k];
               const unsigned long long cand = av & ~nb1;
-              mc[k] = close2_ok ? (cand & a1) : 0ull;
               mg[k] = store2 ? (cand & ~a1) : 0ull;
               snb2[slot * W + k] = nb1 | av;
+              // closings of t+2 vertices: hashed in place
+              unsigned long long cb = close2_ok ? (cand & a1) : 0ull;
+              while (cb) {
+                const unsigned int w = 64u * k + __ffsll((long long)cb) - 1;
+                cb &= cb - 1;
+                ++ncyc2;
+                hacc += mix64(hv + rtab[w] + gam2);
+              }
             }
             sh2[slot] = hv;
             sv12[slot] = v1;
           }
         }
 #pragma unroll
-        for (int k = 0; k < W; ++k) {
-          scl2[slot * W + k] = mc[k];
-          sch2[slot * W + k] = mg[k];
-        }
+        for (int k = 0; k < W; ++k) sch2[slot * W + k] = mg[k];
       }
       __syncwarp();
-      work2(scl2, false);
-      if (store2) work2(sch2, true);
+      if (store2) list2_children();
     }
   };
 
@@ -921,10 +920,9 @@ __device__ __forceinline__ void process_multi_flat(const EngineParams& p, const 
   run.key = 0xFFFFFFFFu;
   const unsigned long long T = (unsigned long long)gridDim.x * blockDim.x;
 
-  auto flush_children = [&](unsigned int n) {
+  // children entries [0, n) take slots base + [0, n)
+  auto flush_children = [&](unsigned int n, unsigned long long base) {
     __syncwarp();
-    unsigned long long base = 0;
-    if (lane == 0) base = atomicAdd(&p.ctl->cnt[s % 3], (unsigned long long)n);
     base = __shfl_sync(0xffffffffu, base, 0);
     for (unsigned int i = lane; i < n; i += 32) {
       const unsigned int e = sl[i], pj = e >> 8, v = e & 0xFFu;
@@ -978,6 +976,10 @@ __device__ __forceinline__ void process_multi_flat(const EngineParams& p, const 
       if (lane >= (unsigned)o) incl += y;
     }
     const unsigned int excl = incl - cnt, total = __shfl_sync(0xffffffffu, incl, 31);
+    // a child list's slots: one atomic, issued before the listing so that its round trip
+    // overlaps it
+    unsigned long long base = 0;
+    if (children && total && lane == 0) base = atomicAdd(&p.ctl->cnt[s % 3], (unsigned long long)total);
     for (unsigned int c0 = 0; c0 < total; c0 += CL) {
       if (cnt && excl < c0 + CL && excl + cnt > c0) {
         unsigned int idx = excl;
@@ -992,7 +994,7 @@ __device__ __forceinline__ void process_multi_flat(const EngineParams& p, const 
           }
         }
       }
-      if (children) flush_children(min(CL, total - c0));
+      if (children) flush_children(min(CL, total - c0), base + c0);
       else flush_closings(min(CL, total - c0));
     }
   };
