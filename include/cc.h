@@ -88,8 +88,10 @@ typedef struct cc_options {
   uint32_t paths_per_thread;   /* bitset and batch expansion: paths a thread takes per    */
                                /* round, 1..3; 0 = the build's default for the path       */
   uint32_t small_phase_paths;  /* bitset graphs: the cluster phase expands levels (or     */
-                               /* chunks) of at most this many paths; 0 = 2 * cluster     */
-                               /* size * 1024                                            */
+                               /* chunks) of at most this many paths.  0 = 2 * cluster    */
+                               /* size * 1024 for graphs of maximum degree <= 5, and no   */
+                               /* cluster phase for denser ones; a nonzero value runs     */
+                               /* the phase for every bitset graph                        */
 } cc_options;
 
 /* cc_options.flags */

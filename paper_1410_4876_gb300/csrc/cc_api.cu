@@ -344,8 +344,11 @@ extern "C" cc_status cc_enumerate(cc_graph* g, uint32_t max_len, uint64_t* out_h
   };
   // small levels first on one thread-block cluster (hardware barrier between levels),
   // then the persistent grid resumes from the state it leaves
+  // (by default only for sparse graphs: with more children per path the phase's per-lane
+  // loops are slower than the persistent grid's flattened form)
   int cs = 0;
-  if (!is_csr(kind) && !(c->opts.flags & CC_FLAG_NO_CLUSTER_PHASE)) {
+  if (!is_csr(kind) && !(c->opts.flags & CC_FLAG_NO_CLUSTER_PHASE) &&
+      (c->opts.small_phase_paths != 0 || p.maxch <= kClusterSparseMaxch)) {
     const unsigned long long key = (unsigned long long)kind | ((unsigned long long)smem << 8);
     cs = -1;
     for (auto& kv : c->cluster_sizes)

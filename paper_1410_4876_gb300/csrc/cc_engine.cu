@@ -96,6 +96,9 @@ __device__ __forceinline__ unsigned long long record_bytes(unsigned int t_child)
 // however fast the levels grow: the per-step floor (barrier and counter round trips) and
 // the frontier traffic of the skipped level outweigh the staging cost.
 constexpr unsigned int kFuseSparseMaxch = 4;
+// The cluster phase's two-level form (one path per lane) is used up to this many bitset
+// words (wider rows would spill registers at 1024 threads per block).
+constexpr int kFuseLaneMaxW = 1;
 
 template <Kind K>
 __device__ bool plan_step(const EngineParams& p, LocalState& st, StepPlan& pl) {
@@ -132,7 +135,8 @@ __device__ bool plan_step(const EngineParams& p, LocalState& st, StepPlan& pl) {
     // unless the graph is sparse, only while the frontier grows by at most 1.3x per level
     // (measured: in denser graphs, steps of fast-growing levels are quicker one level at a
     // time).
-    if (p.fuse_ok && !p.cluster && t + 1 < p.L && f.cursor == 0 && f.next != kNoNext && f.next > 0 &&
+    if (p.fuse_ok && (!p.cluster || (KindTraits<K>::W <= kFuseLaneMaxW && f.next <= p.handover)) && t + 1 < p.L &&
+        f.cursor == 0 && f.next != kNoNext && f.next > 0 &&
         (f.next * 10ull <= f.count * 13ull || p.maxch <= kFuseSparseMaxch)) {
       const unsigned long long need2 = (t + 2 < p.L) ? f.next * p.maxch : 0ull;
       const unsigned long long rb2 = record_bytes<K>(t + 2);
@@ -489,6 +493,130 @@ __device__ __forceinline__ void process_bitset(const EngineParams& p, const Step
     if (nx) atomicAdd(&nxtp[s % 3], nx);
     if (!MULTI && ncyc) atomicAdd(&p.hist[t + 1], ncyc);
     if (!MULTI && hacc) atomicAdd(p.hash, hacc);
+  }
+}
+
+// Two levels in one step, one path per lane (the small cluster phase, single graph).
+// Each lane expands its path p (closings of t+1 vertices hashed), then each child
+// p' = <p, v> in place: its closings (t+2 vertices) are hashed and its children are
+// counted; after one slot atomic per warp, the children are walked again and the
+// grandchildren <p', w> stored with B'' = B | Adj(vt) | Adj(v), H'' = H + r(v) + r(w) and
+// their exact child counts.  Level t+1 is neither stored nor read back.  The lanes'
+// loops are uneven, but the levels of this phase are small and their cost is the step
+// floor, which this form pays once for two levels.
+template <Kind K>
+__device__ __forceinline__ void process_bitset_fused_lane(const EngineParams& p, const StepPlan& pl,
+                                                          const unsigned long long* adj,
+                                                          const unsigned long long* rtab, unsigned long long* s_red,
+                                                          unsigned long long* cntp, unsigned long long* nxtp) {
+  constexpr int W = KindTraits<K>::W;
+  const unsigned int tid = threadIdx.x, lane = tid & 31;
+  const unsigned long long ss = pl.src_stride, ds = pl.dst_stride;
+  const unsigned long long* sB = reinterpret_cast<const unsigned long long*>(p.arena + pl.src_base);
+  const unsigned long long* sH = sB + W * ss;
+  const unsigned int* sM = reinterpret_cast<const unsigned int*>(sH + ss);
+  unsigned long long* dB = reinterpret_cast<unsigned long long*>(p.arena + pl.dst_base);
+  unsigned long long* dH = dB + W * ds;
+  unsigned int* dM = reinterpret_cast<unsigned int*>(dH + ds);
+  const unsigned int t = pl.t, L = p.L;
+  const unsigned long long s = pl.s;
+  // a two-level step has t + 1 < L': the children are within the bound
+  const bool close2_ok = t + 2 <= L, store2 = ds != 0, next_ok = t + 3 < L;
+  const unsigned long long gam1 = (unsigned long long)(t + 1) * kGamma, gam2 = (unsigned long long)(t + 2) * kGamma;
+  unsigned long long nx = 0, ncyc1 = 0, ncyc2 = 0, hacc = 0;
+  const unsigned long long T = (unsigned long long)gridDim.x * blockDim.x;
+  const unsigned long long gwarp = ((unsigned long long)(tid >> 5) * gridDim.x + blockIdx.x) * 32ull;
+  for (unsigned long long wb = pl.begin + gwarp; wb < pl.end; wb += T) {
+    const unsigned long long i = wb + lane;
+    const bool valid = i < pl.end;
+    unsigned long long nb1[W], a1[W], ch1[W];
+    const unsigned long long H = valid ? ldcg64(sH + i) : 0ull;
+    const unsigned int M = valid ? ldcg32(sM + i) : 0u;
+    const unsigned int v1 = M & 0xFFFFu, vt = M >> 16;
+#pragma unroll
+    for (int k = 0; k < W; ++k) {
+      const unsigned long long B = valid ? ldcg64(sB + k * ss + i) : ~0ull;
+      const unsigned long long at = adj[(unsigned long long)vt * W + k];
+      a1[k] = adj[(unsigned long long)v1 * W + k];
+      const unsigned long long cand = at & ~B;
+      ch1[k] = cand & ~a1[k];
+      nb1[k] = B | at;
+      unsigned long long cb = cand & a1[k];
+      while (cb) {
+        const unsigned int v = 64u * k + __ffsll((long long)cb) - 1;
+        cb &= cb - 1;
+        ++ncyc1;
+        hacc += mix64(H + rtab[v] + gam1);
+      }
+    }
+    // the children: closings of t+2 vertices, and their children counted
+    unsigned int ngc = 0;
+#pragma unroll
+    for (int k = 0; k < W; ++k) {
+      unsigned long long b = ch1[k];
+      while (b) {
+        const unsigned int v = 64u * k + __ffsll((long long)b) - 1;
+        b &= b - 1;
+        const unsigned long long hv = H + rtab[v];
+#pragma unroll
+        for (int q = 0; q < W; ++q) {
+          const unsigned long long cand2 = adj[(unsigned long long)v * W + q] & ~nb1[q];
+          unsigned long long cb = close2_ok ? (cand2 & a1[q]) : 0ull;
+          while (cb) {
+            const unsigned int w = 64u * q + __ffsll((long long)cb) - 1;
+            cb &= cb - 1;
+            ++ncyc2;
+            hacc += mix64(hv + rtab[w] + gam2);
+          }
+          ngc += __popcll(cand2 & ~a1[q]);
+        }
+      }
+    }
+    if (!store2) continue;  // warp-uniform
+    unsigned long long slot = warp_slots(ngc, &cntp[s % 3]);
+    if (ngc == 0) continue;
+#pragma unroll
+    for (int k = 0; k < W; ++k) {
+      unsigned long long b = ch1[k];
+      while (b) {
+        const unsigned int v = 64u * k + __ffsll((long long)b) - 1;
+        b &= b - 1;
+        const unsigned long long hv = H + rtab[v];
+        unsigned long long nb2[W];
+#pragma unroll
+        for (int q = 0; q < W; ++q) nb2[q] = nb1[q] | adj[(unsigned long long)v * W + q];
+#pragma unroll
+        for (int q = 0; q < W; ++q) {
+          unsigned long long g = adj[(unsigned long long)v * W + q] & ~nb1[q] & ~a1[q];
+          while (g) {
+            const unsigned int w = 64u * q + __ffsll((long long)g) - 1;
+            g &= g - 1;
+            if (slot < ds) {
+#pragma unroll
+              for (int r = 0; r < W; ++r) {
+                dB[r * ds + slot] = nb2[r];
+                if (next_ok) nx += __popcll(adj[(unsigned long long)w * W + r] & ~nb2[r] & ~a1[r]);
+              }
+              dH[slot] = hv + rtab[w];
+              dM[slot] = v1 | (w << 16);
+            } else {
+              set_err(p.ctl, kDevBounds, 5);
+            }
+            ++slot;
+          }
+        }
+      }
+    }
+  }
+  block_sum3_u64(nx, ncyc1, hacc, s_red);
+  __syncthreads();
+  unsigned long long z0 = 0, z1 = 0;
+  block_sum3_u64(ncyc2, z0, z1, s_red);
+  if (tid == 0) {
+    if (nx) atomicAdd(&nxtp[s % 3], nx);
+    if (ncyc1) atomicAdd(&p.hist[t + 1], ncyc1);
+    if (ncyc2) atomicAdd(&p.hist[t + 2], ncyc2);
+    if (hacc) atomicAdd(p.hash, hacc);
   }
 }
 
@@ -1781,9 +1909,16 @@ __global__ void __launch_bounds__(NT, NT >= 1024 ? 1 : KindTraits<K>::minB) engi
       else process_csr_long(p, pl, nrow, ncol, rtab, s_warp, s_red, &s_base);
     } else {
       // the flattened form for the persistent grid (the small cluster phase keeps the
-      // per-lane form: its levels are small and its 32 warps per block would need 4x the
+      // per-lane forms: its levels are small and its 32 warps per block would need 4x the
       // staging memory)
-      if constexpr (NT >= 1024) process_bitset<K>(p, pl, adj, rtab, s_warp, s_red, &s_base, cntp, nxtp);
+      if constexpr (NT >= 1024) {
+        if constexpr (KindTraits<K>::W <= kFuseLaneMaxW) {
+          if (pl.fuse) process_bitset_fused_lane<K>(p, pl, adj, rtab, s_red, cntp, nxtp);
+          else process_bitset<K>(p, pl, adj, rtab, s_warp, s_red, &s_base, cntp, nxtp);
+        } else {
+          process_bitset<K>(p, pl, adj, rtab, s_warp, s_red, &s_base, cntp, nxtp);
+        }
+      }
       else if constexpr (KindTraits<K>::multi) process_multi_flat<NT>(p, pl, adj, rtab);
       else if (pl.fuse) process_bitset_fused<K, NT>(p, pl, adj, rtab, s_red);
       else process_bitset_flat<K, NT>(p, pl, adj, rtab, s_red);

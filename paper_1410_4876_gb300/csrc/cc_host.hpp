@@ -185,6 +185,10 @@ inline cc_status ensure_arena(cc_context* c) {
   return CC_OK;
 }
 
+// The cluster phase runs by default for graphs with at most this many children per path
+// (maximum degree - 1); cc_options.small_phase_paths != 0 turns it on for every bitset graph.
+constexpr unsigned int kClusterSparseMaxch = 4;
+
 inline int engine_grid(cc_context* c, Kind kind, int block, size_t smem) {
   int bps = 0;
   if (engine_occupancy(kind, block, smem, &bps) != cudaSuccess) {

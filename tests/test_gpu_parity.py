@@ -320,16 +320,38 @@ def test_cluster_phase_equals_grid_only(cc):
     # switching that phase off must not change any result
     graphs = [I.grid(6, 6), I.grid(8, 8), I.gnp(60, 0.15, 7), I.wheel(100), I.gnp(100, 2.4 / 100, 100),
               I.complete_bipartite(8, 8)] + _small_graphs(40, 606)
-    # (one level per step on both sides, so the step counts compare)
-    with cc.Context(frontier_bytes=2 << 30, flags=cc.CC_FLAG_NO_FUSE) as a, \
+    # (one level per step on both sides, so the step counts compare; a nonzero phase size
+    # runs the phase for dense graphs too)
+    with cc.Context(frontier_bytes=2 << 30, flags=cc.CC_FLAG_NO_FUSE, small_phase_paths=32768) as a, \
             cc.Context(frontier_bytes=2 << 30, flags=cc.CC_FLAG_NO_CLUSTER_PHASE | cc.CC_FLAG_NO_FUSE) as b:
         for g in graphs:
             ra, rb = a.enumerate(g), b.enumerate(g)
             assert ra.hist.tolist() == rb.hist.tolist() and ra.hash == rb.hash
             assert ra.tcount.tolist() == rb.tcount.tolist()
             assert ra.info.steps == rb.info.steps
+            assert ra.info.launches == rb.info.launches + 1  # the cluster launch
         for g in graphs[6:]:
             _same(a.enumerate(g), oracle.enumerate_cycles(g))
+
+
+def test_cluster_phase_two_level_steps(cc):
+    # the cluster phase's per-lane two-level form (sparse graphs): same results as the grid
+    # alone, in fewer steps; dense graphs skip the phase unless its size is given
+    sparse = [I.grid(5, 5), I.grid(6, 6), I.grid(6, 7), I.grid(4, 12), I.cycle(40), I.wheel(5)]
+    with cc.Context(frontier_bytes=2 << 30) as a, \
+            cc.Context(frontier_bytes=2 << 30, flags=cc.CC_FLAG_NO_CLUSTER_PHASE) as b, \
+            cc.Context(frontier_bytes=2 << 30, flags=cc.CC_FLAG_NO_FUSE) as u:
+        for g in sparse:
+            ra, rb, ru = a.enumerate(g), b.enumerate(g), u.enumerate(g)
+            ref = oracle.enumerate_cycles(g)
+            _same(ra, ref)
+            _same(rb, ref)
+            assert ra.info.launches == rb.info.launches + 1
+            assert ra.info.steps <= ru.info.steps
+        ra = a.enumerate(I.grid(6, 6))
+        assert ra.info.steps < u.enumerate(I.grid(6, 6)).info.steps
+        g = I.gnp(60, 0.15, 7)
+        assert a.enumerate(g).info.launches == b.enumerate(g).info.launches
 
 
 def test_trace_matches_level_counts(cc, ctx):
