@@ -16,8 +16,9 @@
 // warp's child list its slots with one atomic, accumulate cycles.
 //
 // Expansion forms: process_bitset_flat / process_bitset_fused (one graph, bitset
-// adjacency), process_multi_flat (batch and serving), process_bitset (the small-level
-// cluster phase), process_csr_coop / process_csr_last / process_csr_long (CSR adjacency).
+// adjacency), process_multi_flat (batch and serving), process_bitset /
+// process_bitset_fused_lane (the small-level cluster phase), process_csr_coop /
+// process_csr_last / process_csr_long_thread / process_csr_long_warp (CSR adjacency).
 #include <cooperative_groups.h>
 
 #include "cc_internal.cuh"
@@ -1673,10 +1674,11 @@ __device__ __forceinline__ void process_csr_last(const EngineParams& p, const St
   }
 }
 
-// The same expansion for paths longer than 32 vertices, one thread per path, the path
-// read from its record in the frontier each time it is needed (long chordless paths are
-// rare and their frames small).
-__device__ __forceinline__ void process_csr_long(const EngineParams& p, const StepPlan& pl, const unsigned int* nrow,
+// The same expansion for paths of 33..64 vertices, one thread per path, the path read
+// from its record in the frontier each time it is needed: at these lengths a level may
+// hold millions of paths, and a path per thread keeps more of them in flight than the
+// warp-per-path form below.
+__device__ __forceinline__ void process_csr_long_thread(const EngineParams& p, const StepPlan& pl, const unsigned int* nrow,
                                                  const unsigned short* ncol, const unsigned long long* rtab,
                                                  unsigned int* s_warp, unsigned long long* s_red,
                                                  unsigned long long* s_base) {
@@ -1765,6 +1767,220 @@ __device__ __forceinline__ void process_csr_long(const EngineParams& p, const St
             }
             ++slot;
           }
+        }
+      }
+    }
+  }
+  block_sum3_u64(ncyc, hacc, nbound, s_red);
+  if (threadIdx.x == 0) {
+    if (ncyc) atomicAdd(&p.hist[t + 1], ncyc);
+    if (hacc) atomicAdd(p.hash, hacc);
+    if (nbound) atomicAdd(&p.ctl->nxt[s % 3], nbound);
+  }
+}
+
+// Set the u16 at position e (0..7) of a 16-byte chunk of ids.
+__device__ __forceinline__ void chunk_set_u16(uint4& c, unsigned int e, unsigned int v) {
+  const unsigned int sh = (e & 1u) * 16u, m = 0xFFFFu << sh, x = (v & 0xFFFFu) << sh;
+  switch (e >> 1) {
+    case 0: c.x = (c.x & ~m) | x; break;
+    case 1: c.y = (c.y & ~m) | x; break;
+    case 2: c.z = (c.z & ~m) | x; break;
+    default: c.w = (c.w & ~m) | x; break;
+  }
+}
+
+// True if any u16 of the chunk equals w (a zero 16-bit lane of c ^ ww marks an equal id).
+__device__ __forceinline__ bool chunk_has_u16(const uint4& c, unsigned int ww) {
+  auto z = [](unsigned int x) { return (x - 0x00010001u) & ~x & 0x80008000u; };
+  return (z(c.x ^ ww) | z(c.y ^ ww) | z(c.z ^ ww) | z(c.w ^ ww)) != 0u;
+}
+
+// Candidates with more neighbours than this are tested against the path by looking the
+// path up in their row, not by listing their neighbours as queries.
+constexpr unsigned int kLongQueryMaxDeg = 32;
+// Paths of up to this many vertices take the per-thread long form.
+constexpr unsigned int kLongThreadMaxT = 64;
+
+// True if the sorted row holds x (binary search).
+__device__ __forceinline__ bool row_has(const unsigned short* row, unsigned int d, unsigned int x) {
+  unsigned int lo = 0, hi = d;
+  while (lo < hi) {
+    const unsigned int mid = (lo + hi) >> 1, y = row[mid];
+    if (y == x) return true;
+    if (y < x) lo = mid + 1;
+    else hi = mid;
+  }
+  return false;
+}
+
+// The same expansion for paths of more than 64 vertices, one warp per path.  The record
+// is read in coalesced 16-byte chunks (lane l takes chunks l, l + 32, ...).  A round takes
+// up to 32 candidates v in Adj(vt) (one per lane, label test and v != v_{t-1}).  A
+// candidate of low degree lists its neighbours w >= v2 other than vt and v1 as queries
+// ("is w an interior vertex?"), and one pass of the warp over the record answers every
+// query of the round (queries in shared memory, hits OR-reduced over the lanes).  A
+// candidate of high degree is tested the other way round: every interior vertex is
+// looked up in its sorted row (binary search, the warp's lanes over the record), and v1
+// too.  A candidate without a chord closes a cycle if v1 is its neighbour (hash: the
+// path's r-sum, a warp sum, plus r(v)), and is otherwise a child, copied chunk by chunk
+// with its id appended.
+__device__ __forceinline__ void process_csr_long_warp(const EngineParams& p, const StepPlan& pl,
+                                                      const unsigned int* nrow, const unsigned short* ncol,
+                                                      const unsigned long long* rtab, unsigned long long* s_red) {
+  constexpr unsigned int QC = 32;  // queries per pass
+  __shared__ unsigned int s_q[kMaxThreads / 32][QC];
+  __shared__ unsigned char s_own[kMaxThreads / 32][QC];
+  const unsigned int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  unsigned int* sq = s_q[wid];
+  unsigned char* so = s_own[wid];
+  const unsigned int t = pl.t, L = p.L;
+  const unsigned int R = csr_rec_u16(t), R2 = csr_rec_u16(t + 1), NC = R / 8, NC2 = R2 / 8;
+  const unsigned short* S = reinterpret_cast<const unsigned short*>(p.arena + pl.src_base);
+  unsigned short* D = reinterpret_cast<unsigned short*>(p.arena + pl.dst_base);
+  const unsigned long long ds = pl.dst_stride;
+  const bool store = ds != 0;
+  const bool close_ok = t + 1 <= L, bound_ok = t + 2 < L;
+  const unsigned long long s = pl.s;
+  const unsigned long long gam = (unsigned long long)(t + 1) * kGamma;
+  unsigned long long ncyc = 0, hacc = 0, nbound = 0;
+  const unsigned long long nw = (unsigned long long)gridDim.x * (blockDim.x >> 5);
+  // warp w of block b takes the (w * gridDim + b)-th path, so the warps of a small level
+  // land on different SMs
+  const unsigned long long gw = (unsigned long long)wid * gridDim.x + blockIdx.x;
+  for (unsigned long long i = pl.begin + gw; i < pl.end; i += nw) {  // warp-uniform
+    const unsigned short* rec = S + i * R;
+    const uint4* rc = reinterpret_cast<const uint4*>(rec);
+    const unsigned int v1 = ldcg16(rec), v2 = ldcg16(rec + 1), vp = ldcg16(rec + t - 2), vt = ldcg16(rec + t - 1);
+    const unsigned int rb = nrow[vt], deg = nrow[vt + 1] - rb;
+    bool have_h = false;
+    unsigned long long hsum = 0;
+    for (unsigned int c0 = 0; c0 < deg; c0 += 32) {
+      const unsigned int q = c0 + lane;
+      const unsigned int v = q < deg ? (unsigned int)ncol[rb + q] : 0xFFFFFFFFu;
+      const bool cand = q < deg && v > v2 && v != vp;
+      // this candidate's queries
+      bool close = false;
+      unsigned int nq = 0, eb = 0, ee = 0;
+      if (cand) {
+        eb = nrow[v];
+        ee = nrow[v + 1];
+      }
+      const bool big = cand && ee - eb > kLongQueryMaxDeg;
+      if (cand && !big) {
+        for (unsigned int e = eb; e < ee; ++e) {
+          const unsigned int w = ncol[e];
+          if (w < v2 || w == vt) continue;
+          if (w == v1) close = true;
+          else ++nq;
+        }
+      }
+      unsigned int incl = nq;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const unsigned int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= (unsigned)o) incl += y;
+      }
+      const unsigned int off = incl - nq, qtot = __shfl_sync(0xffffffffu, incl, 31);
+      bool chord = false;
+      for (unsigned int q0 = 0; q0 < qtot; q0 += QC) {
+        if (nq && off < q0 + QC && off + nq > q0) {
+          unsigned int k = off;
+          for (unsigned int e = eb; e < ee; ++e) {
+            const unsigned int w = ncol[e];
+            if (w < v2 || w == vt || w == v1) continue;
+            if (k >= q0 && k < q0 + QC) {
+              sq[k - q0] = w;
+              so[k - q0] = (unsigned char)lane;
+            }
+            ++k;
+          }
+        }
+        __syncwarp();
+        const unsigned int nqc = min(QC, qtot - q0);
+        unsigned int hit = 0;
+        for (unsigned int c = lane; c < NC; c += 32) {
+          const uint4 x = __ldcg(rc + c);
+          for (unsigned int qq = 0; qq < nqc; ++qq) {
+            const unsigned int w = sq[qq];
+            if (chunk_has_u16(x, w | (w << 16))) hit |= 1u << qq;
+          }
+        }
+        hit = __reduce_or_sync(0xffffffffu, hit);
+        while (hit) {
+          const unsigned int qq = __ffs(hit) - 1;
+          hit &= hit - 1;
+          if (so[qq] == lane) chord = true;
+        }
+        __syncwarp();
+      }
+      // high-degree candidates, one at a time: interior vertices looked up in the row
+      unsigned int bm = __ballot_sync(0xffffffffu, big);
+      while (bm) {
+        const unsigned int src = __ffs(bm) - 1;
+        bm &= bm - 1;
+        const unsigned int bb = __shfl_sync(0xffffffffu, eb, src), bd = __shfl_sync(0xffffffffu, ee, src) - bb;
+        const unsigned short* row = ncol + bb;
+        bool found = false;
+        for (unsigned int c = lane; c < NC && !found; c += 32) {
+          const uint4 x = __ldcg(rc + c);
+          const unsigned int u[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+          for (int k = 0; k < 8; ++k) {
+            const unsigned int pos = 8u * c + k;
+            if (pos >= 1 && pos + 1 < t && row_has(row, bd, (u[k >> 1] >> (16 * (k & 1))) & 0xFFFFu)) found = true;
+          }
+        }
+        const bool any = __any_sync(0xffffffffu, found);
+        if (lane == src) {
+          chord = any;
+          close = row_has(row, bd, v1);
+        }
+      }
+      const bool closes = cand && !chord && close;
+      const bool child = cand && !chord && !close && store;
+      if (close_ok && __any_sync(0xffffffffu, closes)) {
+        if (!have_h) {  // the path's r-sum, once per path
+          unsigned long long h = 0;
+          for (unsigned int c = lane; c < NC; c += 32) {
+            const uint4 x = __ldcg(rc + c);
+            const unsigned int u[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+            for (int k = 0; k < 8; ++k)
+              if (8u * c + k < t) h += rtab[(u[k >> 1] >> (16 * (k & 1))) & 0xFFFFu];
+          }
+          hsum = warp_sum_u64(h);
+          have_h = true;
+        }
+        if (closes) {
+          ++ncyc;
+          hacc += mix64(hsum + rtab[v] + gam);
+          if (p.cyc_vert)
+            emit_cycle(p, t + 1, [&](unsigned int j) -> unsigned int {
+              return j < t ? (unsigned int)ldcg16(rec + j) : v;
+            });
+        }
+      }
+      const unsigned int cm = __ballot_sync(0xffffffffu, child);
+      if (cm == 0) continue;
+      unsigned long long base = 0;
+      if (lane == 0) base = atomicAdd(&p.ctl->cnt[s % 3], (unsigned long long)__popc(cm));
+      base = __shfl_sync(0xffffffffu, base, 0);
+      if (child && bound_ok) nbound += nrow[v + 1] - nrow[v] - 1;
+      unsigned int rest = cm;
+      for (unsigned long long slot = base; rest; ++slot) {  // one child at a time, warp-wide copy
+        const unsigned int src = __ffs(rest) - 1;
+        rest &= rest - 1;
+        const unsigned int cv = __shfl_sync(0xffffffffu, v, src);
+        if (slot < ds) {
+          uint4* out = reinterpret_cast<uint4*>(D + slot * R2);
+          for (unsigned int c = lane; c < NC2; c += 32) {
+            uint4 x = c < NC ? __ldcg(rc + c) : make_uint4(0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu);
+            if (c == t / 8) chunk_set_u16(x, t % 8, cv);
+            out[c] = x;
+          }
+        } else if (lane == 0) {
+          set_err(p.ctl, kDevBounds, 2);
         }
       }
     }
@@ -1906,7 +2122,8 @@ __global__ void __launch_bounds__(NT, NT >= 1024 ? 1 : KindTraits<K>::minB) engi
         process_csr_last<(CAP >= 32 ? 32 : 16)>(p, pl, nrow, ncol, nsig, rtab);
       else if (pl.t <= 16) process_csr_coop<16>(p, pl, nrow, ncol, nsig, rtab);
       else if (CAP >= 32 && pl.t <= 32) process_csr_coop<(CAP >= 32 ? 32 : 16)>(p, pl, nrow, ncol, nsig, rtab);
-      else process_csr_long(p, pl, nrow, ncol, rtab, s_warp, s_red, &s_base);
+      else if (pl.t <= kLongThreadMaxT) process_csr_long_thread(p, pl, nrow, ncol, rtab, s_warp, s_red, &s_base);
+      else process_csr_long_warp(p, pl, nrow, ncol, rtab, s_red);
     } else {
       // the flattened form for the persistent grid (the small cluster phase keeps the
       // per-lane forms: its levels are small and its 32 warps per block would need 4x the

@@ -150,6 +150,24 @@ def test_csr_mode_equals_bitset_mode(cc):
             _same(r, oracle.enumerate_cycles(g))
 
 
+def test_csr_long_paths(cc):
+    # paths of more than 32 vertices take the warp-per-path CSR form: forced CSR mode on
+    # graphs with long chordless cycles, cycle lists included
+    with cc.Context(frontier_bytes=1 << 30, mode=cc.CC_MODE_CSR) as c:
+        for g in [I.cycle(100), I.wheel(80), I.gnm(120, 135, 3)]:
+            r = c.enumerate(g, cycles=True)
+            ref = oracle.enumerate_cycles(g, cycles=True)
+            assert r.info.mode == cc.CC_MODE_CSR and max(len(x) for x in ref.cycles) > 33
+            assert sorted(r.cycles) == sorted(ref.cycles)
+            _same(r, ref)
+        # 58547 of the 86350 chordless cycles of the 4 x 16 grid have more than 33 vertices
+        g = I.grid(4, 16)
+        _same(c.enumerate(g), oracle.enumerate_cycles(g))
+        # length bounds inside the long form: closings up to L', no path stored at L'
+        for L in (34, 40):
+            _same(c.enumerate(g, max_len=L), oracle.enumerate_cycles(g, max_len=L))
+
+
 def test_cycle_lists(ctx):
     for g in _small_graphs(40, 7) + [I.grid(4, 5), I.wheel(9), I.complete(6), I.cycle(40)]:
         r = ctx.enumerate(g, cycles=True)
