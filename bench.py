@@ -6,7 +6,7 @@ Erdos-Renyi graph G(n=60, p=0.15, seed 7), all cycle lengths, through the C ABI
 flushed by writing a 256 MiB buffer (about twice the L2).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload grid8+gnp60|grid6|gnm2000|batch]
+                  [--workload grid8+gnp60|grid6|grid7x10|grid8x10|gnm2000|batch|serve|stream]
 
 --impl reference times the CPU oracle (Algorithm 1 in plain C, test infrastructure) on
 the host cores for the same workload and metric.  Under torchrun (N > 1) every rank runs
@@ -391,6 +391,57 @@ def run_batch(args):
     print(json.dumps(line), flush=True)
 
 
+def run_stream(args):
+    """Every cycle of Table 1's 8 x 10 grid (71.5 M, counted without being stored in the
+    paper) listed through cc_enumerate_stream: device lists of --stream-chunk cycles, each
+    round's lists copied to pinned host memory and handed to a sink that checks them
+    (cycle count and length histogram).  Wall time of the whole call, sink included."""
+    import torch
+
+    from paper_1410_4876_gb300 import cc
+    g = I.grid(8, 10)
+    chunk_c = args.stream_chunk
+    chunk_v = 24 * chunk_c
+    ctx = cc.Context(frontier_bytes=_frontier_bytes(args, 32 << 10))
+    lg = ctx.load(g)
+    ref = lg.enumerate()
+    acc = {"cycles": 0, "verts": 0}
+
+    def sink(starts, lengths, verts):
+        acc["cycles"] += len(lengths)
+        acc["verts"] += int(lengths.sum(dtype=np.int64))
+
+    for _ in range(args.warmup):
+        lg.enumerate_stream(sink, 0, chunk_c, chunk_v)
+    torch.cuda.synchronize()
+    times = []
+    rounds = 0
+    for _ in range(args.steps):
+        acc["cycles"] = acc["verts"] = 0
+        t0 = time.perf_counter()
+        r, rounds = lg.enumerate_stream(sink, 0, chunk_c, chunk_v)
+        times.append(time.perf_counter() - t0)
+        assert acc["cycles"] == r.total == ref.total and r.hash == ref.hash
+        assert acc["verts"] == sum(k * int(c) for k, c in enumerate(r.hist))
+    t = min(times)
+    t_count = ref.info.ms_total / 1000.0
+    out_bytes = 12 * acc["cycles"] + 4 * acc["verts"]
+    line = {
+        "metric": "streamed chordless cycles/s", "value": acc["cycles"] / t, "unit": "cycles/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * t, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": "grid 8x10 (80 vertices, 142 edges), every chordless cycle listed "
+                               "(Table 1's count-only row)", "cycles": acc["cycles"], "vertices": acc["verts"],
+                   "chunk_cycles": chunk_c, "chunk_vertices": chunk_v},
+        "rounds": rounds, "steps_expansion": int(r.info.steps), "engine_ms": r.info.ms_engine,
+        "host_bytes_per_s": out_bytes / t, "bytes_to_host": out_bytes,
+        "count_only": {"value": ref.total / t_count, "unit": "cycles/s", "ms": 1000 * t_count},
+    }
+    lg.close()
+    ctx.close()
+    print(json.dumps(line), flush=True)
+
+
 def run_serve(args):
     """Poisson arrivals (seed 3) of serving requests, continuous batching, p50/p99."""
     import torch
@@ -497,7 +548,7 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="grid8+gnp60", choices=sorted(WORKLOADS) + ["batch", "serve"])
+    ap.add_argument("--workload", default="grid8+gnp60", choices=sorted(WORKLOADS) + ["batch", "serve", "stream"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the cpu_baseline leg")
     ap.add_argument("--frontier-mb", type=int, default=0,
                     help="device memory for paths in flight (MiB); 0 = 8 GiB for single graphs, "
@@ -509,11 +560,14 @@ def main():
     ap.add_argument("--serve-seconds", type=float, default=10.0, help="serving: arrival window (s)")
     ap.add_argument("--serve-steps", type=int, default=8, help="serving: expansion steps per round")
     ap.add_argument("--seq-sample", type=int, default=2000, help="serving: requests timed one by one")
+    ap.add_argument("--stream-chunk", type=int, default=32 << 20, help="stream: device list capacity (cycles)")
     args = ap.parse_args()
     if args.workload == "batch":
         return run_batch(args)
     if args.workload == "serve":
         return run_serve(args)
+    if args.workload == "stream":
+        return run_stream(args)
     desc, make = WORKLOADS[args.workload]
     work = make()
     if args.impl == "reference":

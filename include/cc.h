@@ -201,6 +201,36 @@ cc_status cc_enumerate(cc_graph* g, uint32_t max_len, uint64_t* out_hist, uint64
                        uint64_t* out_tcount, cc_cycles* out_cycles, cc_run_info* out_info);
 
 /*
+ * Streamed cycle lists.  Table 1 of the paper counts the 71.5 M cycles of the 8 x 10 grid
+ * without storing them, and Section 6 leaves a transport between host and GPU memory to
+ * future work; this call lists every cycle of any size of output through bounded device
+ * buffers.  The enumeration runs in rounds: a round stops when the next step could
+ * overflow the device list (the planner takes at most as many paths in a step as the
+ * list's room holds, a path closing at most max_degree - 1 cycles of t + 1 vertices),
+ * the round's cycles are copied to pinned host memory and passed to `sink`, and the
+ * engine resumes from the state it left.  The CSR path is used (as for cc_cycles).
+ *   chunk_cycles, chunk_vertices  device list capacity per round (cycles, vertices); at
+ *                 least max(max_degree - 1, (max_degree - 1) m / 2) and
+ *                 max((max_degree - 1) (L' + 1), 3 (max_degree - 1) m / 2), else CC_ERR_ARG.
+ *                 Device memory: 12 chunk_cycles + 4 chunk_vertices bytes for the call,
+ *                 and the same in pinned host memory, kept by the context for reuse.
+ *   sink(user, count, starts, lengths, vertices, total_vertices)  called on the calling
+ *                 thread after each round with cycles: cycle i is vertices[starts[i] ..
+ *                 starts[i] + lengths[i]) in the canonical order of cc_cycles (original
+ *                 ids, smallest first, then towards its smaller neighbour).  Cycles come in
+ *                 no particular order.  The arrays are valid during the call only.
+ *   out_hist, out_hash, out_tcount, out_info  as for cc_enumerate; out_rounds (or NULL):
+ *                 the number of rounds.
+ * Errors: those of cc_enumerate, and CC_ERR_ARG for a NULL sink or capacities below the
+ * minimum.  Never CC_ERR_TRUNCATED unless the list bound is broken (a bug).
+ */
+typedef void (*cc_cycle_sink)(void* user, uint64_t count, const uint64_t* starts, const uint32_t* lengths,
+                              const uint32_t* vertices, uint64_t total_vertices);
+cc_status cc_enumerate_stream(cc_graph* g, uint32_t max_len, uint64_t chunk_cycles, uint64_t chunk_vertices,
+                              cc_cycle_sink sink, void* user, uint64_t* out_hist, uint64_t* out_hash,
+                              uint64_t* out_tcount, uint32_t* out_rounds, cc_run_info* out_info);
+
+/*
  * CUDA graphs (the paper relaunches its kernels from the host, Algorithm 4; here a whole
  * call is one replayable unit).  Without out_cycles and without CC_FLAG_NO_GRAPH, the
  * second cc_enumerate of a graph with the same max_len and launch configuration captures

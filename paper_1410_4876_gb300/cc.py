@@ -136,6 +136,9 @@ SIGNATURES = {
     "cc_batch_poll": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32, _u64p, ctypes.c_uint32,
                                        _u64p, _u64p, _dblp, ctypes.POINTER(cc_run_info)]),
     "cc_get_trace": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_uint32, _u64p, _u64p, _u64p]),
+    "cc_enumerate_stream": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_uint64,
+                                             ctypes.c_void_p, ctypes.c_void_p, _u64p, _u64p, _u64p, _u32p,
+                                             ctypes.POINTER(cc_run_info)]),
     "cc_context_set_options": (ctypes.c_int32, [ctypes.c_void_p, ctypes.POINTER(cc_options)]),
     "cc_tune": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_uint32, ctypes.c_char_p, ctypes.POINTER(cc_tune_result)]),
     "cc_tune_batch": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_uint32, _u32p, _u64p, _u32p, _u64p, _u32p,
@@ -263,6 +266,41 @@ def cc_enumerate(g, n: int, max_len: int = 0, tcount: bool = True, cycles_capaci
         elif s == CC_ERR_TRUNCATED:
             out_cycles = (int(cyc.count), int(cyc.total_vertices))
     return s, hist, int(hsh.value), tc, out_cycles, info
+
+
+# void sink(void* user, uint64_t count, const uint64_t* starts, const uint32_t* lengths,
+#           const uint32_t* vertices, uint64_t total_vertices)
+CYCLE_SINK = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_uint64, _u64p, _u32p, _u32p, ctypes.c_uint64)
+
+
+def cc_enumerate_stream(g, n: int, sink, max_len: int = 0, chunk_cycles: int = 1 << 20,
+                        chunk_vertices: int = 1 << 24):
+    """Streamed cycle list.  ``sink(starts, lengths, vertices)`` receives each round's
+    cycles as numpy views (valid during the call only): cycle i is
+    vertices[starts[i]:starts[i] + lengths[i]].  Returns (status, hist, hash, tcount,
+    rounds, info)."""
+    L = n if (max_len == 0 or max_len > n) else max_len
+    hist = np.zeros(L + 1, dtype=np.uint64)
+    tc = np.zeros(L + 1, dtype=np.uint64)
+    hsh = ctypes.c_uint64(0)
+    rounds = ctypes.c_uint32(0)
+    info = cc_run_info()
+    err = []
+
+    def _sink(user, count, starts, lengths, vertices, nv):
+        try:
+            sink(np.ctypeslib.as_array(starts, (count,)), np.ctypeslib.as_array(lengths, (count,)),
+                 np.ctypeslib.as_array(vertices, (nv,)))
+        except BaseException as x:  # an exception cannot cross the C frame: re-raised below
+            err.append(x)
+
+    cb = CYCLE_SINK(_sink)
+    s = load_library().cc_enumerate_stream(g, max_len, chunk_cycles, chunk_vertices, ctypes.cast(cb, ctypes.c_void_p),
+                                           None, _p64(hist), ctypes.byref(hsh), _p64(tc), ctypes.byref(rounds),
+                                           ctypes.byref(info))
+    if err:
+        raise err[0]
+    return s, hist, int(hsh.value), tc, int(rounds.value), info
 
 
 def cc_batch_submit(ctx, graphs: Sequence, max_len: int = 0):
@@ -398,6 +436,15 @@ class LoadedGraph:
                 continue
             _check(s, "cc_enumerate")
             return Result(hist, h, tc, cyc, info)
+
+    def enumerate_stream(self, sink, max_len: int = 0, chunk_cycles: int = 1 << 20,
+                         chunk_vertices: int = 1 << 24):
+        """Every cycle through ``sink(starts, lengths, vertices)``, round by round (see
+        cc_enumerate_stream); returns (Result without cycles, rounds)."""
+        s, hist, h, tc, rounds, info = cc_enumerate_stream(self.handle, self.n, sink, max_len, chunk_cycles,
+                                                           chunk_vertices)
+        _check(s, "cc_enumerate_stream")
+        return Result(hist, h, tc, None, info), rounds
 
     def tune(self, max_len: int = 0, cache_path: Optional[str] = None) -> cc_tune_result:
         s, out = cc_tune(self.handle, max_len, cache_path)

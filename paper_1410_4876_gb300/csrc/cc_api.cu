@@ -94,6 +94,7 @@ extern "C" void cc_context_destroy(cc_context* c) {
   if (c->own_arena && c->arena) cudaFree(c->arena);
   if (c->h_res) cudaFreeHost(c->h_res);
   if (c->h_ctl) cudaFreeHost(c->h_ctl);
+  if (c->h_stream) cudaFreeHost(c->h_stream);
   if (c->ev0) cudaEventDestroy(c->ev0);
   if (c->ev1) cudaEventDestroy(c->ev1);
   if (c->ev2) cudaEventDestroy(c->ev2);
@@ -202,8 +203,17 @@ extern "C" cc_status cc_graph_info(const cc_graph* g, uint32_t* n, uint64_t* m, 
 
 // ------------------------------------------------------------------ enumerate
 
-extern "C" cc_status cc_enumerate(cc_graph* g, uint32_t max_len, uint64_t* out_hist, uint64_t* out_hash,
-                                  uint64_t* out_tcount, cc_cycles* out_cycles, cc_run_info* out_info) {
+namespace {
+// A streamed cycle list (cc_enumerate_stream): device list capacities per round and the sink.
+struct StreamOut {
+  unsigned long long cap_c, cap_v;
+  cc_cycle_sink sink;
+  void* user;
+  uint32_t rounds;
+};
+
+cc_status enumerate_impl(cc_graph* g, uint32_t max_len, uint64_t* out_hist, uint64_t* out_hash, uint64_t* out_tcount,
+                         cc_cycles* out_cycles, StreamOut* so, cc_run_info* out_info) {
   if (!g || !out_hist || !out_hash) return CC_ERR_ARG;
   if (out_cycles && ((out_cycles->capacity_cycles && !out_cycles->offsets) ||
                      (out_cycles->capacity_vertices && !out_cycles->vertices)))
@@ -220,8 +230,9 @@ extern "C" cc_status cc_enumerate(cc_graph* g, uint32_t max_len, uint64_t* out_h
   // path choice: the bitset path needs n <= 256; the cycle list needs ordered paths (CSR)
   Kind kind;
   const unsigned int mode = c->opts.mode;
-  if (mode == CC_MODE_BITSET && (g->W == 0 || out_cycles)) return CC_ERR_UNSUPPORTED;
-  if (out_cycles || mode == CC_MODE_CSR || g->W == 0)
+  const bool listing = out_cycles || so;
+  if (mode == CC_MODE_BITSET && (g->W == 0 || listing)) return CC_ERR_UNSUPPORTED;
+  if (listing || mode == CC_MODE_CSR || g->W == 0)
     kind = L <= 17 ? Kind::Csr16 : (L <= 33 ? Kind::Csr32 : Kind::Csr);  // stored paths have < L' vertices
   else kind = g->W == 1 ? Kind::Bitset1 : (g->W == 2 ? Kind::Bitset2 : Kind::Bitset4);
   info.mode = is_csr(kind) ? CC_MODE_CSR : CC_MODE_BITSET;
@@ -243,14 +254,29 @@ extern "C" cc_status cc_enumerate(cc_graph* g, uint32_t max_len, uint64_t* out_h
   unsigned int* d_cv = nullptr;
   unsigned long long* d_cs = nullptr;
   unsigned int* d_cl = nullptr;
-  const unsigned long long capc = out_cycles ? out_cycles->capacity_cycles : 0;
-  const unsigned long long capv = out_cycles ? out_cycles->capacity_vertices : 0;
+  const unsigned long long capc = so ? so->cap_c : (out_cycles ? out_cycles->capacity_cycles : 0);
+  const unsigned long long capv = so ? so->cap_v : (out_cycles ? out_cycles->capacity_vertices : 0);
   auto free_cyc = [&]() {
     dev_free(c, d_cv);
     dev_free(c, d_cs);
     dev_free(c, d_cl);
   };
-  if (out_cycles) {
+  // (streamed lists: every round must have room for one path's worst case, maxch cycles of
+  // up to L' vertices, and the first round for the triangles, at most (Delta - 1) m / 2)
+  const unsigned long long maxch = std::max(1u, g->maxdeg > 0 ? g->maxdeg - 1 : 1u);
+  const unsigned long long tri = g->maxdeg > 1 ? (unsigned long long)(g->maxdeg - 1) * g->m / 2 : 0;
+  if (so && (capc < std::max(maxch, tri) || capv < std::max(maxch * (L + 1), 3 * tri))) return CC_ERR_ARG;
+  if (so) {
+    const size_t hb = 12 * capc + 4 * capv;
+    if (c->h_stream_bytes < hb) {
+      if (c->h_stream) cudaFreeHost(c->h_stream);
+      c->h_stream = nullptr;
+      c->h_stream_bytes = 0;
+      CC_CUDA(cudaMallocHost((void**)&c->h_stream, hb));
+      c->h_stream_bytes = hb;
+    }
+  }
+  if (listing) {
     if ((s = dev_alloc(c, (void**)&d_cv, 4 * std::max(capv, 1ull))) ||
         (s = dev_alloc(c, (void**)&d_cs, 8 * std::max(capc, 1ull))) ||
         (s = dev_alloc(c, (void**)&d_cl, 4 * std::max(capc, 1ull)))) {
@@ -298,6 +324,7 @@ extern "C" cc_status cc_enumerate(cc_graph* g, uint32_t max_len, uint64_t* out_h
   p.cyc_len = d_cl;
   p.cyc_cap_c = capc;
   p.cyc_cap_v = capv;
+  p.cyc_stream = so ? 1u : 0u;
   // frame 0 (initial triplets) sized by |T(G)| <= (Delta - 1) m / 2 (Section 2)
   unsigned long long tb = g->maxdeg > 1 ? (unsigned long long)(g->maxdeg - 1) * g->m / 2 + 8 : 8;
   const unsigned long long seed_stride = round_up(tb, 8);
@@ -388,7 +415,7 @@ extern "C" cc_status cc_enumerate(cc_graph* g, uint32_t max_len, uint64_t* out_h
     rec(c->ev2);
   };
   // CUDA graph: the key covers everything the captured work depends on
-  const bool use_graph = !out_cycles && !(c->opts.flags & CC_FLAG_NO_GRAPH) && !g->no_graph;
+  const bool use_graph = !listing && !(c->opts.flags & CC_FLAG_NO_GRAPH) && !g->no_graph;
   unsigned long long gkey = 0;
   if (use_graph) {
     const unsigned long long parts[] = {(unsigned long long)kind, (unsigned long long)grid, (unsigned long long)block,
@@ -435,6 +462,46 @@ extern "C" cc_status cc_enumerate(cc_graph* g, uint32_t max_len, uint64_t* out_h
     issue();
   }
   ok(cudaStreamSynchronize(st));
+  // streamed cycle list: drain the round's cycles to the sink, reset the list counters and
+  // resume the engine from the state it left, until no frame is left
+  cc_status ss = CC_OK;
+  while (so && e == cudaSuccess) {
+    const Control& hc = *c->h_ctl;
+    so->rounds += 1;
+    if (hc.err != 0) break;
+    if (hc.cyc_count > capc || hc.cyc_verts > capv) {  // (the planner's bound prevents this)
+      ss = CC_ERR_TRUNCATED;
+      break;
+    }
+    const unsigned long long nc = hc.cyc_count, nv = hc.cyc_verts;
+    if (nc) {
+      uint64_t* hs = reinterpret_cast<uint64_t*>(c->h_stream);
+      uint32_t* hl = reinterpret_cast<uint32_t*>(hs + capc);
+      uint32_t* hv = hl + capc;
+      ok(cudaMemcpyAsync(hs, d_cs, 8 * nc, cudaMemcpyDeviceToHost, st));
+      ok(cudaMemcpyAsync(hl, d_cl, 4 * nc, cudaMemcpyDeviceToHost, st));
+      ok(cudaMemcpyAsync(hv, d_cv, 4 * nv, cudaMemcpyDeviceToHost, st));
+      ok(cudaStreamSynchronize(st));
+      if (e != cudaSuccess) break;
+      so->sink(so->user, nc, hs, hl, hv, nv);
+    }
+    if (hc.depth == 0) break;
+    if (nc == 0 && so->rounds > 1 && hc.step == info.steps) {  // no progress (cannot happen)
+      ss = CC_ERR_CAPACITY;
+      break;
+    }
+    info.steps = hc.step;
+    EngineParams q = p;
+    q.fresh = 0;
+    ok(cudaMemsetAsync(&c->ctl->cyc_count, 0, 2 * sizeof(unsigned long long), st));
+    ok(launch_engine(kind, q, grid, block, smem, st));
+    info.launches += 1;
+    rec(c->ev1);
+    ok(cudaMemcpyAsync(c->h_res, c->d_res, words * 8, cudaMemcpyDeviceToHost, st));
+    ok(cudaMemcpyAsync(c->h_ctl, c->ctl, sizeof(Control), cudaMemcpyDeviceToHost, st));
+    rec(c->ev2);
+    ok(cudaStreamSynchronize(st));
+  }
   if (e != cudaSuccess) {
     (void)cudaGetLastError();
     free_cyc();
@@ -451,6 +518,7 @@ extern "C" cc_status cc_enumerate(cc_graph* g, uint32_t max_len, uint64_t* out_h
   info.ms_engine = ms3;
   const Control& h = *c->h_ctl;
   s = map_dev_err(h.err);
+  if (s == CC_OK) s = ss;
   std::memcpy(out_hist, c->h_res, sizeof(uint64_t) * (L + 1));
   if (out_tcount) std::memcpy(out_tcount, c->h_res + (L + 1), sizeof(uint64_t) * (L + 1));
   *out_hash = c->h_res[2 * (L + 1)];
@@ -497,6 +565,23 @@ extern "C" cc_status cc_enumerate(cc_graph* g, uint32_t max_len, uint64_t* out_h
   free_cyc();
   c->last = info;
   if (out_info) *out_info = info;
+  return s;
+}
+}  // namespace
+
+extern "C" cc_status cc_enumerate(cc_graph* g, uint32_t max_len, uint64_t* out_hist, uint64_t* out_hash,
+                                  uint64_t* out_tcount, cc_cycles* out_cycles, cc_run_info* out_info) {
+  return enumerate_impl(g, max_len, out_hist, out_hash, out_tcount, out_cycles, nullptr, out_info);
+}
+
+extern "C" cc_status cc_enumerate_stream(cc_graph* g, uint32_t max_len, uint64_t chunk_cycles,
+                                         uint64_t chunk_vertices, cc_cycle_sink sink, void* user, uint64_t* out_hist,
+                                         uint64_t* out_hash, uint64_t* out_tcount, uint32_t* out_rounds,
+                                         cc_run_info* out_info) {
+  if (!sink) return CC_ERR_ARG;
+  StreamOut so{chunk_cycles, chunk_vertices, sink, user, 0};
+  const cc_status s = enumerate_impl(g, max_len, out_hist, out_hash, out_tcount, nullptr, &so, out_info);
+  if (out_rounds) *out_rounds = so.rounds;
   return s;
 }
 

@@ -112,10 +112,21 @@ __device__ bool plan_step(const EngineParams& p, LocalState& st, StepPlan& pl) {
   const Frame& f = st.cur;
   const unsigned long long rem = f.count - f.cursor;
   const unsigned int t = f.t;
-  unsigned long long need;
+  unsigned long long need, lim = rem;
   if constexpr (KindTraits<K>::csr) {
+    if (p.cyc_stream && t + 1 <= p.L) {
+      // streamed cycle list: a path closes at most maxch cycles of t+1 vertices, so the step
+      // takes no more paths than the list's room holds; with no room it stops here and the
+      // host drains the list and resumes (the counters are final after the barrier)
+      const unsigned long long uc = ld_relaxed_u64(&p.ctl->cyc_count), uv = ld_relaxed_u64(&p.ctl->cyc_verts);
+      const unsigned long long rc = uc < p.cyc_cap_c ? (p.cyc_cap_c - uc) / p.maxch : 0ull;
+      const unsigned long long rv =
+          uv < p.cyc_cap_v ? (p.cyc_cap_v - uv) / ((unsigned long long)p.maxch * (t + 1)) : 0ull;
+      lim = min(lim, min(rc, rv));
+      if (lim == 0) return false;
+    }
     // CSR frames carry an upper bound on their children (sum of deg(v_t) - 1)
-    need = (t + 1 < p.L) ? ((f.cursor == 0 && f.next != kNoNext) ? f.next : rem * p.maxch) : 0ull;
+    need = (t + 1 < p.L) ? ((f.cursor == 0 && f.next != kNoNext && lim == rem) ? f.next : lim * p.maxch) : 0ull;
   } else if constexpr (KindTraits<K>::multi) {
     need = (f.cursor == 0 && f.next != kNoNext) ? f.next : rem * p.maxch;
   } else {
@@ -123,7 +134,7 @@ __device__ bool plan_step(const EngineParams& p, LocalState& st, StepPlan& pl) {
   }
   const unsigned long long res = KindTraits<K>::multi ? p.reserve : 0ull;
   unsigned long long cap = need + (need || res ? res : 0ull);
-  st.chunk = rem;
+  st.chunk = lim;
   st.has_child = 0;
   st.fused = 0;
   pl.fuse = 0;
@@ -186,7 +197,7 @@ __device__ bool plan_step(const EngineParams& p, LocalState& st, StepPlan& pl) {
         set_err(p.ctl, kDevCapacity, (int)t);
         return false;
       }
-      if (ch < rem) {
+      if (ch < st.chunk) {
         st.chunk = ch;
         if (blockIdx.x == 0) p.ctl->spilled = 1;
       }

@@ -46,6 +46,8 @@ struct cc_context {
   cc_run_info last{};
   std::vector<std::pair<unsigned long long, int>> cluster_sizes;  // (kind | smem << 8) -> size
   unsigned long long last_t_start = 0;  // globaltimer at the start of the last expansion
+  unsigned char* h_stream = nullptr;    // pinned drain buffer of streamed cycle lists
+  size_t h_stream_bytes = 0;
   // batch state
   struct Batch {
     cc_batch_id id = 0;

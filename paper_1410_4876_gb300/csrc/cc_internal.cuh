@@ -151,6 +151,8 @@ struct EngineParams {
   unsigned long long handover;     // cluster phase: stop before expanding more paths than this
   unsigned int pf;                 // bitset / batch: paths per thread per round (1..P of the kind)
   unsigned int fuse_ok;            // one graph, bitset, persistent grid: two-level steps allowed
+  unsigned int cyc_stream;         // CSR cycle list drained between launches: a step takes no
+                                   // more paths than the list's room allows, none when it is full
 };
 
 #ifdef __CUDACC__
