@@ -18,7 +18,7 @@
 // Expansion forms: process_bitset_flat / process_bitset_fused (one graph, bitset
 // adjacency), process_multi_flat (batch and serving), process_bitset /
 // process_bitset_fused_lane (the small-level cluster phase), process_csr_coop /
-// process_csr_last / process_csr_long_thread / process_csr_long_warp (CSR adjacency).
+// process_csr_last / process_csr_long_warp (CSR adjacency).
 #include <cooperative_groups.h>
 
 #include "cc_internal.cuh"
@@ -1256,8 +1256,9 @@ __device__ __forceinline__ bool on_path(const unsigned int* row, unsigned int nw
   return any != 0;
 }
 
-// Per-warp shared memory of the CSR loops (one copy per block and CAP): staged rows,
-// child list, queued exact tests.
+// Per-warp shared memory of the CSR loops: staged rows, child list, queued exact tests.
+// One buffer per block, sized for the kind's largest CAP, serves every CAP (a step runs
+// one form, and steps are separated by barriers).
 template <int CAP>
 struct CsrSmem {
   static constexpr int RS = CAP / 2 + 1;
@@ -1265,13 +1266,18 @@ struct CsrSmem {
   unsigned int child[kMaxThreads / 32][128];
   unsigned int exact[kMaxThreads / 32][64];
 };
-template <int CAP>
+template <int MAXCAP>
+__device__ __forceinline__ unsigned char* csr_smem_raw() {
+  __shared__ __align__(16) unsigned char raw[sizeof(CsrSmem<MAXCAP>)];
+  return raw;
+}
+template <int CAP, int MAXCAP>
 __device__ __forceinline__ CsrSmem<CAP>& csr_smem() {
-  __shared__ CsrSmem<CAP> sm;
-  return sm;
+  static_assert(CAP <= MAXCAP, "a CSR form's staging must fit the kind's buffer");
+  return *reinterpret_cast<CsrSmem<CAP>*>(csr_smem_raw<MAXCAP>());
 }
 
-template <int CAP>
+template <int CAP, int MAXCAP>
 __device__ __forceinline__ void process_csr_coop(const EngineParams& p, const StepPlan& pl,
                                                  const unsigned int* nrow, const unsigned short* ncol,
                                                  const unsigned long long* nsig, const unsigned long long* rtab) {
@@ -1279,7 +1285,7 @@ __device__ __forceinline__ void process_csr_coop(const EngineParams& p, const St
   constexpr int NQ = CAP / 8;               // uint4 per staged row
   constexpr unsigned int CL = 128;          // child list entries per warp
   constexpr unsigned int CX = 64;           // queued exact tests per warp
-  CsrSmem<CAP>& sm = csr_smem<CAP>();
+  CsrSmem<CAP>& sm = csr_smem<CAP, MAXCAP>();
   const unsigned int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const unsigned int lt_mask = (1u << lane) - 1u;
   unsigned int* sp = sm.path[wid];
@@ -1513,13 +1519,13 @@ __device__ __forceinline__ void process_csr_coop(const EngineParams& p, const St
 // rows, and every 32 queued paths are expanded together: flattened (path, candidate)
 // pairs, v1's bit in nsig(v) first, then v1 in Adj(v) (sorted row) and, for a closing,
 // the chord test of Adj(v) against the staged ids.
-template <int CAP>
+template <int CAP, int MAXCAP>
 __device__ __forceinline__ void process_csr_last(const EngineParams& p, const StepPlan& pl,
                                                  const unsigned int* nrow, const unsigned short* ncol,
                                                  const unsigned long long* nsig, const unsigned long long* rtab) {
   constexpr int NP = CAP / 2, RS = NP + 1, NQ = CAP / 8;
   constexpr unsigned int CX = 64;
-  CsrSmem<CAP>& sm = csr_smem<CAP>();
+  CsrSmem<CAP>& sm = csr_smem<CAP, MAXCAP>();
   const unsigned int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const unsigned int lt_mask = (1u << lane) - 1u;
   unsigned int* sq = sm.path[wid];  // queued rows
@@ -1685,111 +1691,6 @@ __device__ __forceinline__ void process_csr_last(const EngineParams& p, const St
   }
 }
 
-// The same expansion for paths of 33..64 vertices, one thread per path, the path read
-// from its record in the frontier each time it is needed: at these lengths a level may
-// hold millions of paths, and a path per thread keeps more of them in flight than the
-// warp-per-path form below.
-__device__ __forceinline__ void process_csr_long_thread(const EngineParams& p, const StepPlan& pl, const unsigned int* nrow,
-                                                 const unsigned short* ncol, const unsigned long long* rtab,
-                                                 unsigned int* s_warp, unsigned long long* s_red,
-                                                 unsigned long long* s_base) {
-  const unsigned int tid = threadIdx.x;
-  const unsigned int t = pl.t, L = p.L;
-  const unsigned int R = csr_rec_u16(t), R2 = csr_rec_u16(t + 1);
-  const unsigned short* S = reinterpret_cast<const unsigned short*>(p.arena + pl.src_base);
-  unsigned short* D = reinterpret_cast<unsigned short*>(p.arena + pl.dst_base);
-  const unsigned long long ds = pl.dst_stride;
-  const bool store = ds != 0;
-  const bool close_ok = t + 1 <= L, bound_ok = t + 2 < L;
-  const unsigned long long s = pl.s;
-  unsigned long long ncyc = 0, hacc = 0, nbound = 0;
-  for (unsigned long long t0 = pl.begin + (unsigned long long)blockIdx.x * blockDim.x; t0 < pl.end;
-       t0 += (unsigned long long)gridDim.x * blockDim.x) {
-    const unsigned long long i = t0 + tid;
-    const bool valid = i < pl.end;
-    const unsigned short* rec = S + i * R;
-    unsigned int v1 = 0xFFFFu, v2 = 0xFFFFu, vt = 0, vp = 0, rb = 0, deg = 0;
-    unsigned long long sig = 0;
-    if (valid) {
-      v1 = ldcg16(rec);
-      v2 = ldcg16(rec + 1);
-      vt = ldcg16(rec + t - 1);
-      vp = ldcg16(rec + t - 2);
-      for (unsigned int k = 1; k + 1 < t; ++k) sig |= 1ull << (ldcg16(rec + k) & 63u);
-      rb = nrow[vt];
-      deg = nrow[vt + 1] - rb;
-    }
-    for (unsigned int w0 = 0; __syncthreads_or(valid && w0 < deg); w0 += 32) {
-      unsigned int mask = 0;
-      if (valid && w0 < deg) {
-        const unsigned int qend = min(deg, w0 + 32);
-        for (unsigned int q = w0; q < qend; ++q) {
-          const unsigned int v = ncol[rb + q];
-          if (v <= v2 || v == vp) continue;
-          bool close = false, chord = false;
-          const unsigned int e1 = nrow[v + 1];
-          for (unsigned int e = nrow[v]; e < e1 && !chord; ++e) {
-            const unsigned int w = ncol[e];
-            if (w < v2 || w == vt) continue;
-            if (w == v1) {
-              close = true;
-              continue;
-            }
-            if ((sig >> (w & 63u)) & 1ull)
-              for (unsigned int k = 1; k + 1 < t; ++k)
-                if (ldcg16(rec + k) == w) {
-                  chord = true;
-                  break;
-                }
-          }
-          if (chord) continue;
-          if (close) {
-            if (close_ok) {
-              ++ncyc;
-              unsigned long long hs = rtab[v];
-              for (unsigned int k = 0; k < t; ++k) hs += rtab[ldcg16(rec + k)];
-              hacc += mix64(hs + (unsigned long long)(t + 1) * kGamma);
-              if (p.cyc_vert)
-                emit_cycle(p, t + 1, [&](unsigned int j) -> unsigned int {
-                  return j < t ? (unsigned int)ldcg16(rec + j) : v;
-                });
-            }
-          } else if (store) {
-            mask |= 1u << (q - w0);
-          }
-        }
-      }
-      if (store) {
-        const unsigned long long off = tile_slots(__popc(mask), &p.ctl->cnt[s % 3], s_warp, s_base);
-        if (mask) {
-          unsigned long long slot = off;
-          while (mask) {
-            const unsigned int q = __ffs(mask) - 1;
-            mask &= mask - 1;
-            const unsigned int v = ncol[rb + w0 + q];
-            if (slot < ds) {
-              unsigned short* out = D + slot * R2;
-              for (unsigned int k = 0; k < t; ++k) out[k] = ldcg16(rec + k);
-              out[t] = (unsigned short)v;
-              for (unsigned int k = t + 1; k < R2; ++k) out[k] = 0xFFFFu;
-              if (bound_ok) nbound += nrow[v + 1] - nrow[v] - 1;
-            } else {
-              set_err(p.ctl, kDevBounds, 2);
-            }
-            ++slot;
-          }
-        }
-      }
-    }
-  }
-  block_sum3_u64(ncyc, hacc, nbound, s_red);
-  if (threadIdx.x == 0) {
-    if (ncyc) atomicAdd(&p.hist[t + 1], ncyc);
-    if (hacc) atomicAdd(p.hash, hacc);
-    if (nbound) atomicAdd(&p.ctl->nxt[s % 3], nbound);
-  }
-}
-
 // Set the u16 at position e (0..7) of a 16-byte chunk of ids.
 __device__ __forceinline__ void chunk_set_u16(uint4& c, unsigned int e, unsigned int v) {
   const unsigned int sh = (e & 1u) * 16u, m = 0xFFFFu << sh, x = (v & 0xFFFFu) << sh;
@@ -1810,8 +1711,6 @@ __device__ __forceinline__ bool chunk_has_u16(const uint4& c, unsigned int ww) {
 // Candidates with more neighbours than this are tested against the path by looking the
 // path up in their row, not by listing their neighbours as queries.
 constexpr unsigned int kLongQueryMaxDeg = 32;
-// Paths of up to this many vertices take the per-thread long form.
-constexpr unsigned int kLongThreadMaxT = 64;
 
 // True if the sorted row holds x (binary search).
 __device__ __forceinline__ bool row_has(const unsigned short* row, unsigned int d, unsigned int x) {
@@ -2127,13 +2026,14 @@ __global__ void __launch_bounds__(NT, NT >= 1024 ? 1 : KindTraits<K>::minB) engi
     __syncthreads();
     if (pl.done) break;
     if constexpr (KindTraits<K>::csr) {
-      constexpr int CAP = KindTraits<K>::cap;
-      if (pl.dst_stride == 0 && pl.t <= 16) process_csr_last<16>(p, pl, nrow, ncol, nsig, rtab);
-      else if (pl.dst_stride == 0 && CAP >= 32 && pl.t <= 32)
-        process_csr_last<(CAP >= 32 ? 32 : 16)>(p, pl, nrow, ncol, nsig, rtab);
-      else if (pl.t <= 16) process_csr_coop<16>(p, pl, nrow, ncol, nsig, rtab);
-      else if (CAP >= 32 && pl.t <= 32) process_csr_coop<(CAP >= 32 ? 32 : 16)>(p, pl, nrow, ncol, nsig, rtab);
-      else if (pl.t <= kLongThreadMaxT) process_csr_long_thread(p, pl, nrow, ncol, rtab, s_warp, s_red, &s_base);
+      constexpr int CAP = KindTraits<K>::cap;  // ids a staged row holds: 16, 32 or 64
+      constexpr int C32 = CAP >= 32 ? 32 : 16, C64 = CAP >= 64 ? 64 : 16;
+      if (pl.dst_stride == 0 && pl.t <= 16) process_csr_last<16, CAP>(p, pl, nrow, ncol, nsig, rtab);
+      else if (pl.dst_stride == 0 && CAP >= 32 && pl.t <= 32) process_csr_last<C32, CAP>(p, pl, nrow, ncol, nsig, rtab);
+      else if (pl.dst_stride == 0 && CAP >= 64 && pl.t <= 64) process_csr_last<C64, CAP>(p, pl, nrow, ncol, nsig, rtab);
+      else if (pl.t <= 16) process_csr_coop<16, CAP>(p, pl, nrow, ncol, nsig, rtab);
+      else if (CAP >= 32 && pl.t <= 32) process_csr_coop<C32, CAP>(p, pl, nrow, ncol, nsig, rtab);
+      else if (CAP >= 64 && pl.t <= 64) process_csr_coop<C64, CAP>(p, pl, nrow, ncol, nsig, rtab);
       else process_csr_long_warp(p, pl, nrow, ncol, rtab, s_red);
     } else {
       // the flattened form for the persistent grid (the small cluster phase keeps the
