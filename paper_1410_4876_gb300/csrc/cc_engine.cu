@@ -20,6 +20,7 @@
 // process_bitset_fused_lane (the small-level cluster phase), process_csr_coop /
 // process_csr_last / process_csr_long_warp (CSR adjacency).
 #include <cooperative_groups.h>
+#include <cstddef>
 
 #include "cc_internal.cuh"
 
@@ -46,6 +47,10 @@ struct LocalState {
   unsigned long long expanded;  // paths expanded by the planned step (both levels of a fused one)
 };
 
+// (word by word, bypassing L1: another block may have stored the frame)
+static_assert(offsetof(Frame, next) == 40 && offsetof(Frame, ncl) == 48 && offsetof(Frame, t) == 56 &&
+                  offsetof(Frame, end) == 60 && sizeof(Frame) == 64,
+              "load_frame reads the Frame layout word by word");
 __device__ __forceinline__ Frame load_frame(const Frame* f) {
   Frame r;
   const unsigned long long* q = reinterpret_cast<const unsigned long long*>(f);
@@ -55,7 +60,8 @@ __device__ __forceinline__ Frame load_frame(const Frame* f) {
   r.count = __ldcg(q + 3);
   r.cursor = __ldcg(q + 4);
   r.next = __ldcg(q + 5);
-  const unsigned long long te = __ldcg(q + 6);
+  r.ncl = __ldcg(q + 6);
+  const unsigned long long te = __ldcg(q + 7);
   r.t = (unsigned int)(te & 0xFFFFFFFFull);
   r.end = (unsigned int)(te >> 32);
   return r;
@@ -115,15 +121,24 @@ __device__ bool plan_step(const EngineParams& p, LocalState& st, StepPlan& pl) {
   unsigned long long need, lim = rem;
   if constexpr (KindTraits<K>::csr) {
     if (p.cyc_stream && t + 1 <= p.L) {
-      // streamed cycle list: a path closes at most maxch cycles of t+1 vertices, so the step
-      // takes no more paths than the list's room holds; with no room it stops here and the
-      // host drains the list and resumes (the counters are final after the barrier)
+      // streamed cycle list: the step's closings (t+1 vertices each) must fit the list's
+      // room, or the step stops here and the host drains the list and resumes (the list
+      // counters are final after the barrier).  A whole frame with a known closing bound
+      // is taken if the bound fits, and waits for an empty list if only that would hold
+      // it; otherwise a path closes at most maxch cycles and the step takes no more paths
+      // than the room holds at that rate.
       const unsigned long long uc = ld_relaxed_u64(&p.ctl->cyc_count), uv = ld_relaxed_u64(&p.ctl->cyc_verts);
-      const unsigned long long rc = uc < p.cyc_cap_c ? (p.cyc_cap_c - uc) / p.maxch : 0ull;
-      const unsigned long long rv =
-          uv < p.cyc_cap_v ? (p.cyc_cap_v - uv) / ((unsigned long long)p.maxch * (t + 1)) : 0ull;
-      lim = min(lim, min(rc, rv));
-      if (lim == 0) return false;
+      const unsigned long long roomc = uc < p.cyc_cap_c ? p.cyc_cap_c - uc : 0ull;
+      const unsigned long long roomv = uv < p.cyc_cap_v ? p.cyc_cap_v - uv : 0ull;
+      const bool whole = f.cursor == 0 && f.ncl != kNoNext;
+      if (whole && f.ncl <= roomc && f.ncl * (t + 1) <= roomv) {
+        lim = rem;
+      } else if (whole && (uc || uv) && f.ncl <= p.cyc_cap_c && f.ncl * (t + 1) <= p.cyc_cap_v) {
+        return false;
+      } else {
+        lim = min(lim, min(roomc / p.maxch, roomv / ((unsigned long long)p.maxch * (t + 1))));
+        if (lim == 0) return false;
+      }
     }
     // CSR frames carry an upper bound on their children (sum of deg(v_t) - 1)
     need = (t + 1 < p.L) ? ((f.cursor == 0 && f.next != kNoNext && lim == rem) ? f.next : lim * p.maxch) : 0ull;
@@ -168,6 +183,7 @@ __device__ bool plan_step(const EngineParams& p, LocalState& st, StepPlan& pl) {
           c.count = 0;
           c.cursor = 0;
           c.next = kNoNext;
+          c.ncl = kNoNext;
           c.t = t + 2;
           st.has_child = 1;
           st.peak = max(st.peak, p.arena_bytes - (freeb - bytes));
@@ -213,6 +229,7 @@ __device__ bool plan_step(const EngineParams& p, LocalState& st, StepPlan& pl) {
     c.count = 0;
     c.cursor = 0;
     c.next = kNoNext;
+    c.ncl = kNoNext;
     c.t = KindTraits<K>::multi ? 0u : t + 1;
     st.has_child = 1;
     st.peak = max(st.peak, p.arena_bytes - (freeb - bytes));
@@ -230,7 +247,7 @@ __device__ bool plan_step(const EngineParams& p, LocalState& st, StepPlan& pl) {
 
 template <Kind K>
 __device__ void commit_step(const EngineParams& p, LocalState& st, unsigned long long c, unsigned long long nx,
-                            bool writer) {
+                            unsigned long long ncl, bool writer) {
   const unsigned int t = st.cur.t;
   // a two-level step: its children were counted exactly before the step (the frame's next)
   if (st.fused && writer) atomicAdd(&p.tcount[t + 1], st.cur.next);
@@ -251,6 +268,7 @@ __device__ void commit_step(const EngineParams& p, LocalState& st, unsigned long
     g.count = c;
     g.cursor = 0;
     g.next = nx;  // exact (bitset, batch) or an upper bound (CSR)
+    g.ncl = ncl;
     if (g.end) st.top = g.base; else st.bot = g.base + g.bytes;
     if (st.depth >= p.max_depth) {
       set_err(p.ctl, kDevDepth, (int)st.depth);
@@ -1347,6 +1365,16 @@ __device__ __forceinline__ void process_csr_coop(const EngineParams& p, const St
         set_err(p.ctl, kDevBounds, 3);
       }
     }
+    if (p.cyc_stream && t + 2 <= L) {  // streamed lists: the children's closing bound
+      unsigned int k = 0;
+      for (unsigned int j = lane; j < nchild; j += 32) {
+        const unsigned int e = sc[j];
+        const unsigned int* orow = sp + (e >> 16) * RS;
+        k += closing_bound(nrow, ncol, nsig, e & 0xFFFFu, orow[0] & 0xFFFFu, rec_id(orow, t - 1));
+      }
+      k = __reduce_add_sync(0xffffffffu, k);
+      if (lane == 0 && k) atomicAdd(&p.ctl->ncl[s % 3], (unsigned long long)k);
+    }
     nchild = 0;
     __syncwarp();
   };
@@ -1737,7 +1765,8 @@ __device__ __forceinline__ bool row_has(const unsigned short* row, unsigned int 
 // with its id appended.
 __device__ __forceinline__ void process_csr_long_warp(const EngineParams& p, const StepPlan& pl,
                                                       const unsigned int* nrow, const unsigned short* ncol,
-                                                      const unsigned long long* rtab, unsigned long long* s_red) {
+                                                      const unsigned long long* nsig, const unsigned long long* rtab,
+                                                      unsigned long long* s_red) {
   constexpr unsigned int QC = 32;  // queries per pass
   __shared__ unsigned int s_q[kMaxThreads / 32][QC];
   __shared__ unsigned char s_own[kMaxThreads / 32][QC];
@@ -1877,6 +1906,10 @@ __device__ __forceinline__ void process_csr_long_warp(const EngineParams& p, con
       if (lane == 0) base = atomicAdd(&p.ctl->cnt[s % 3], (unsigned long long)__popc(cm));
       base = __shfl_sync(0xffffffffu, base, 0);
       if (child && bound_ok) nbound += nrow[v + 1] - nrow[v] - 1;
+      if (p.cyc_stream && t + 2 <= L) {  // streamed lists: the children's closing bound
+        const unsigned int k = __reduce_add_sync(0xffffffffu, child ? closing_bound(nrow, ncol, nsig, v, v1, vt) : 0u);
+        if (lane == 0 && k) atomicAdd(&p.ctl->ncl[s % 3], (unsigned long long)k);
+      }
       unsigned int rest = cm;
       for (unsigned long long slot = base; rest; ++slot) {  // one child at a time, warp-wide copy
         const unsigned int src = __ffs(rest) - 1;
@@ -1901,6 +1934,7 @@ __device__ __forceinline__ void process_csr_long_warp(const EngineParams& p, con
     if (hacc) atomicAdd(p.hash, hacc);
     if (nbound) atomicAdd(&p.ctl->nxt[s % 3], nbound);
   }
+
 }
 
 // ------------------------------------------------------------------ the persistent kernel
@@ -1993,6 +2027,7 @@ __global__ void __launch_bounds__(NT, NT >= 1024 ? 1 : KindTraits<K>::minB) engi
       st.cur.count = n0;
       st.cur.cursor = 0;
       st.cur.next = c->seed_next;
+      st.cur.ncl = kNoNext;
       st.cur.t = KindTraits<K>::multi ? 0u : 3u;
       st.cur.end = 0;
       if (blockIdx.x == 0) c->t_start = globaltimer();
@@ -2034,7 +2069,7 @@ __global__ void __launch_bounds__(NT, NT >= 1024 ? 1 : KindTraits<K>::minB) engi
       else if (pl.t <= 16) process_csr_coop<16, CAP>(p, pl, nrow, ncol, nsig, rtab);
       else if (CAP >= 32 && pl.t <= 32) process_csr_coop<C32, CAP>(p, pl, nrow, ncol, nsig, rtab);
       else if (CAP >= 64 && pl.t <= 64) process_csr_coop<C64, CAP>(p, pl, nrow, ncol, nsig, rtab);
-      else process_csr_long_warp(p, pl, nrow, ncol, rtab, s_red);
+      else process_csr_long_warp(p, pl, nrow, ncol, nsig, rtab, s_red);
     } else {
       // the flattened form for the persistent grid (the small cluster phase keeps the
       // per-lane forms: its levels are small and its 32 warps per block would need 4x the
@@ -2054,6 +2089,7 @@ __global__ void __launch_bounds__(NT, NT >= 1024 ? 1 : KindTraits<K>::minB) engi
     if (blockIdx.x == 0 && tid == 0) {
       cntp[(s + 1) % 3] = 0;
       nxtp[(s + 1) % 3] = 0;
+      if (p.cyc_stream) p.ctl->ncl[(s + 1) % 3] = 0;
     }
     if (p.cluster) {
       cluster_barrier();
@@ -2073,7 +2109,8 @@ __global__ void __launch_bounds__(NT, NT >= 1024 ? 1 : KindTraits<K>::minB) engi
       // (the cluster phase has no barrier that can time out and a child count is clamped to
       // its frame, so it leaves the error word to the grid phase and to the host)
       const int err = NT >= 1024 ? 0 : ld_relaxed_i32(&p.ctl->err);
-      commit_step<K>(p, st, c, nx, blockIdx.x == 0);
+      const unsigned long long ncl = p.cyc_stream ? ld_relaxed_u64(&p.ctl->ncl[s % 3]) : kNoNext;
+      commit_step<K>(p, st, c, nx, ncl, blockIdx.x == 0);
       if (err != 0) st.depth = 0;  // every block reads the same word: all stop here
       if (blockIdx.x == 0 && p.step_ts && s < p.step_ts_cap) {
         p.step_ts[s] = globaltimer();

@@ -69,6 +69,7 @@ struct Frame {
   unsigned long long count;   // records present
   unsigned long long cursor;  // records already expanded
   unsigned long long next;    // exact number of children of the whole frame, or kNoNext
+  unsigned long long ncl;     // streamed CSR lists: bound on the frame's closings, or kNoNext
   unsigned int t;             // path length (one-graph modes); 0 = per record (batch)
   unsigned int end;           // 0 = bottom stack, 1 = top stack
 };
@@ -83,6 +84,7 @@ constexpr unsigned int kMaxBarGroups = 256;
 struct Control {
   alignas(128) unsigned long long cnt[3];  // children written in step s (index s % 3)
   unsigned long long nxt[3];               // children-of-children of step s (next frame size)
+  unsigned long long ncl[3];               // streamed CSR lists: closing bound of step s's children
   alignas(128) unsigned int bar_gen;       // barrier generation (released by the last group)
   int err;                                 // first device error (kDev*), 0 if none
   int err_info;
@@ -156,6 +158,29 @@ struct EngineParams {
 };
 
 #ifdef __CUDACC__
+// Streamed CSR lists: a bound on the cycles that the child <v1 .. vt, v> closes when it is
+// expanded, |Adj(v) & Adj(v1) \ {vt}| (each closing vertex neighbours both ends).  Sorted
+// rows; disjoint neighbour signatures settle most pairs without reading a row.
+__device__ __forceinline__ unsigned int closing_bound(const unsigned int* nrow, const unsigned short* ncol,
+                                                      const unsigned long long* nsig, unsigned int v,
+                                                      unsigned int v1, unsigned int vt) {
+  if (((nsig[2 * v] & nsig[2 * v1]) | (nsig[2 * v + 1] & nsig[2 * v1 + 1])) == 0) return 0;
+  unsigned int a = nrow[v], ae = nrow[v + 1], b = nrow[v1], be = nrow[v1 + 1], k = 0;
+  while (a < ae && b < be) {
+    const unsigned int x = ncol[a], y = ncol[b];
+    if (x == y) {
+      k += x != vt;
+      ++a;
+      ++b;
+    } else if (x < y) {
+      ++a;
+    } else {
+      ++b;
+    }
+  }
+  return k;
+}
+
 // Cycle list entry in canonical order (original ids): smallest id first, then towards
 // its smaller cycle neighbour.  vtx(j) returns the relabelled id of cycle position j.
 template <typename F>

@@ -389,6 +389,7 @@ extern "C" cc_status cc_serve_step(cc_server* v, cc_completion* out, uint32_t ca
       f.bytes = bitset_region_bytes(stride, 1);
       f.stride = stride;
       f.next = 0;
+      f.ncl = kNoNext;
       Control nc = ctl;
       nc.depth = 1;
       nc.bot = f.bytes;
