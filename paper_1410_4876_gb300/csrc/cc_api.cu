@@ -155,22 +155,31 @@ extern "C" cc_status cc_graph_load(cc_context* c, uint32_t n, const uint32_t* ro
     cc_graph_free(g);
     return st;
   };
-  if ((s = dev_alloc(c, (void**)&g->d_row, 4ull * (n + 1)))) return fail(s);
-  if ((s = dev_alloc(c, (void**)&g->d_col, 4ull * std::max<uint32_t>(row_ptr[n], 1)))) return fail(s);
-  if ((s = dev_alloc(c, (void**)&g->d_perm, 8ull * std::max<uint32_t>(n, 1)))) return fail(s);
-  if ((s = dev_alloc(c, (void**)&g->d_rtab, g->rtab_bytes))) return fail(s);
-  if ((s = dev_alloc(c, (void**)&g->d_nrow, g->nrow_bytes))) return fail(s);
-  if ((s = dev_alloc(c, (void**)&g->d_ncol, g->ncol_bytes))) return fail(s);
-  if ((s = dev_alloc(c, (void**)&g->d_nsig, g->nsig_bytes))) return fail(s);
-  if (g->W && (s = dev_alloc(c, (void**)&g->d_adj, g->adj_bytes))) return fail(s);
-  if (cudaMemcpyAsync(g->d_row, row_ptr, 4ull * (n + 1), cudaMemcpyHostToDevice, c->stream) != cudaSuccess ||
-      (row_ptr[n] && cudaMemcpyAsync(g->d_col, sorted.data(), 4ull * row_ptr[n], cudaMemcpyHostToDevice,
-                                     c->stream) != cudaSuccess) ||
-      cudaMemsetAsync(g->d_nrow, 0, g->nrow_bytes, c->stream) != cudaSuccess ||
-      cudaMemsetAsync(g->d_ncol, 0, g->ncol_bytes, c->stream) != cudaSuccess ||
-      cudaMemsetAsync(g->d_rtab, 0, g->rtab_bytes, c->stream) != cudaSuccess ||
-      cudaMemsetAsync(g->d_nsig, 0, g->nsig_bytes, c->stream) != cudaSuccess ||
-      cudaStreamSynchronize(c->stream) != cudaSuccess) {
+  // every buffer of the graph in one stream-ordered allocation (256-byte aligned parts):
+  // the original CSR first, copied in one transfer, the rest zeroed by one memset
+  auto a256 = [](unsigned long long x) { return (x + 255ull) & ~255ull; };
+  const unsigned long long nnz = row_ptr[n];
+  const unsigned long long o_row = 0, o_col = a256(4ull * (n + 1)), o_perm = a256(o_col + 4ull * std::max(nnz, 1ull));
+  const unsigned long long o_rtab = a256(o_perm + 8ull * std::max<uint32_t>(n, 1)), o_nrow = a256(o_rtab + g->rtab_bytes);
+  const unsigned long long o_ncol = a256(o_nrow + g->nrow_bytes), o_nsig = a256(o_ncol + g->ncol_bytes);
+  const unsigned long long o_adj = a256(o_nsig + g->nsig_bytes), total = a256(o_adj + g->adj_bytes);
+  if ((s = dev_alloc(c, (void**)&g->d_block, total))) return fail(s);
+  unsigned char* b = g->d_block;
+  g->d_row = reinterpret_cast<unsigned int*>(b + o_row);
+  g->d_col = reinterpret_cast<unsigned int*>(b + o_col);
+  g->d_perm = reinterpret_cast<unsigned int*>(b + o_perm);
+  g->d_rtab = reinterpret_cast<unsigned long long*>(b + o_rtab);
+  g->d_nrow = reinterpret_cast<unsigned int*>(b + o_nrow);
+  g->d_ncol = reinterpret_cast<unsigned short*>(b + o_ncol);
+  g->d_nsig = reinterpret_cast<unsigned long long*>(b + o_nsig);
+  g->d_adj = g->W ? reinterpret_cast<unsigned long long*>(b + o_adj) : nullptr;
+  // (from pageable memory: the call returns once the host copy is staged, so the vector
+  // may go; the enumeration on the same stream sees the data)
+  std::vector<uint32_t> up(o_col / 4 + nnz);
+  std::memcpy(up.data(), row_ptr, 4ull * (n + 1));
+  if (nnz) std::memcpy(up.data() + o_col / 4, sorted.data(), 4ull * nnz);
+  if (cudaMemcpyAsync(b, up.data(), 4ull * up.size(), cudaMemcpyHostToDevice, c->stream) != cudaSuccess ||
+      cudaMemsetAsync(b + o_perm, 0, total - o_perm, c->stream) != cudaSuccess) {
     (void)cudaGetLastError();
     return fail(CC_ERR_CUDA);
   }
@@ -181,14 +190,7 @@ extern "C" cc_status cc_graph_load(cc_context* c, uint32_t n, const uint32_t* ro
 extern "C" void cc_graph_free(cc_graph* g) {
   if (!g) return;
   cc_context* c = g->ctx;
-  dev_free(c, g->d_row);
-  dev_free(c, g->d_col);
-  dev_free(c, g->d_perm);
-  dev_free(c, g->d_adj);
-  dev_free(c, g->d_rtab);
-  dev_free(c, g->d_nrow);
-  dev_free(c, g->d_ncol);
-  dev_free(c, g->d_nsig);
+  dev_free(c, g->d_block);
   if (g->exec) cudaGraphExecDestroy(g->exec);
   delete g;
 }

@@ -83,6 +83,7 @@ struct cc_graph {
   unsigned int* d_nrow = nullptr;   // relabelled CSR
   unsigned short* d_ncol = nullptr;
   unsigned long long* d_nsig = nullptr;  // neighbour signatures of the relabelled CSR [2n]
+  unsigned char* d_block = nullptr;      // one allocation holding every buffer above
   size_t nrow_bytes = 0, ncol_bytes = 0, adj_bytes = 0, rtab_bytes = 0, nsig_bytes = 0;
   // captured device work of cc_enumerate for one launch configuration (CUDA graph)
   cudaGraphExec_t exec = nullptr;
