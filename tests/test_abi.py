@@ -73,3 +73,26 @@ def test_struct_layouts_match_header(tmp_path):
         py = structs[name]
         got = ctypes.sizeof(py) if field == "size" else getattr(py, field).offset
         assert got == int(value), (name, field, got, value)
+
+
+def test_null_handles_are_refused_without_a_gpu():
+    # argument checks run before any CUDA call: NULL handles, outputs and sinks give
+    # CC_ERR_ARG on a machine without a GPU
+    from paper_1410_4876_gb300 import cc
+    lib = cc.load_library()
+    u64 = ctypes.c_uint64(0)
+    hist = (ctypes.c_uint64 * 8)()
+    assert lib.cc_enumerate(None, 0, hist, ctypes.byref(u64), None, None, None) == cc.CC_ERR_ARG
+    assert lib.cc_enumerate_stream(None, 0, 1 << 20, 1 << 24, None, None, hist, ctypes.byref(u64), None, None,
+                                   None) == cc.CC_ERR_ARG
+    sink = cc.CYCLE_SINK(lambda *a: None)
+    assert lib.cc_enumerate_stream(None, 0, 1 << 20, 1 << 24, ctypes.cast(sink, ctypes.c_void_p), None, hist,
+                                   ctypes.byref(u64), None, None, None) == cc.CC_ERR_ARG
+    handle = ctypes.c_void_p()
+    rp = (ctypes.c_uint32 * 2)(0, 0)
+    assert lib.cc_graph_load(None, 1, rp, rp, ctypes.byref(handle)) == cc.CC_ERR_ARG
+    assert lib.cc_context_set_options(None, ctypes.byref(cc.cc_options())) == cc.CC_ERR_ARG
+    assert lib.cc_tune(None, 0, None, ctypes.byref(cc.cc_tune_result())) == cc.CC_ERR_ARG
+    assert lib.cc_get_trace(None, 0, None, None, ctypes.byref(u64)) == cc.CC_ERR_ARG
+    lib.cc_graph_free(None)
+    lib.cc_context_destroy(None)
