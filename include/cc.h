@@ -205,10 +205,12 @@ cc_status cc_enumerate(cc_graph* g, uint32_t max_len, uint64_t* out_hist, uint64
  * without storing them, and Section 6 leaves a transport between host and GPU memory to
  * future work; this call lists every cycle of any size of output through bounded device
  * buffers.  The enumeration runs in rounds: a round stops when the next step could
- * overflow the device list (the planner takes at most as many paths in a step as the
- * list's room holds, a path closing at most max_degree - 1 cycles of t + 1 vertices),
- * the round's cycles are copied to pinned host memory and passed to `sink`, and the
- * engine resumes from the state it left.  The CSR path is used (as for cc_cycles).
+ * overflow the device list, the round's cycles are copied to pinned host memory and
+ * passed to `sink`, and the engine resumes from the state it left.  (Each stored level
+ * carries a bound on the cycles its paths close, the sum of |Adj(v) & Adj(v1)| over its
+ * paths; a level whose bound fits the list's room is expanded whole, otherwise a step
+ * takes as many paths as the room holds at max_degree - 1 cycles of t + 1 vertices per
+ * path.)  The CSR path is used (as for cc_cycles).
  *   chunk_cycles, chunk_vertices  device list capacity per round (cycles, vertices); at
  *                 least max(max_degree - 1, (max_degree - 1) m / 2) and
  *                 max((max_degree - 1) (L' + 1), 3 (max_degree - 1) m / 2), else CC_ERR_ARG.
