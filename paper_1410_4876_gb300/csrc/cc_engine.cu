@@ -11,8 +11,9 @@
 // Per step: take the top frame, choose how much of it to expand (all of it if the exact
 // or bounded child count fits the free arena, else the largest chunk that fits; that
 // chunk's subtree then runs depth-first; a bitset level whose children are known exactly
-// and grow slowly is expanded together with them), expand those paths, list their
-// children and closings as (path, vertex) entries worked off one per lane, give each
+// and grow slowly, or any such level of a sparse graph, is expanded together with them;
+// with a streamed cycle list, no more than the list's room can take), expand those
+// paths, list their children as (path, vertex) entries worked off one per lane, give each
 // warp's child list its slots with one atomic, accumulate cycles.
 //
 // Expansion forms: process_bitset_flat / process_bitset_fused (one graph, bitset
