@@ -62,7 +62,7 @@ typedef int32_t cc_status;
 #define CC_ERR_CUDA (-4)          /* a CUDA call failed (no device, launch error, ...)    */
 #define CC_ERR_TIMEOUT (-5)       /* a bounded device wait gave up                        */
 #define CC_ERR_TRUNCATED (-6)     /* cycle list buffer too small; required sizes returned */
-#define CC_ERR_UNSUPPORTED (-7)   /* graph beyond this build's limits (see cc_limits)     */
+#define CC_ERR_UNSUPPORTED (-7)   /* graph beyond the library's limits (see cc_limits)    */
 #define CC_ERR_CAPACITY (-8)      /* frontier memory too small to make progress           */
 
 #define CC_MODE_AUTO 0   /* bitset adjacency when n <= 256, CSR adjacency otherwise */
