@@ -54,6 +54,47 @@ def test_cycle_hash_is_set_function():
     assert oracle.cycle_hash([5, 9, 2, 8]) != h
 
 
+def _splitmix_draw(state: int) -> int:
+    return oracle.splitmix64_next(state)[0]
+
+
+GAMMA = 0x9E3779B97F4A7C15
+MASK = (1 << 64) - 1
+
+
+@pytest.mark.parametrize("cyc", [(0, 1, 2), (3, 5, 8, 9), (7, 1, 4, 0, 12), tuple(range(10, 22))])
+def test_cycle_hash_from_the_published_stream(cyc):
+    # h(C) = mix(sum r(v) + |C| * GAMMA) with r(v) = draw v (0-based) of the seed-0
+    # SplitMix64 stream.  Both sides are built here from the generator alone (pinned by
+    # the published output sequence above): r(v) by drawing v + 1 times from state 0, and
+    # h(C) as the next draw from the state sum r(v) + (|C| - 1) GAMMA, since a draw first
+    # adds GAMMA to the state.  A dropped, doubled or mis-scaled length term fails here.
+    r = {}
+    for v in cyc:
+        s, out = 0, None
+        for _ in range(v + 1):
+            out, s = oracle.splitmix64_next(s)
+        r[v] = out
+    k = len(cyc)
+    state = (sum(r.values()) + (k - 1) * GAMMA) & MASK
+    assert oracle.cycle_hash(list(cyc)) == _splitmix_draw(state)
+    # the length term is really there: the same draw without it differs
+    assert oracle.cycle_hash(list(cyc)) != _splitmix_draw((sum(r.values()) - GAMMA) & MASK)
+
+
+def test_graph_hash_of_single_cycles():
+    # a graph that is one chordless cycle hashes to that cycle's h(C), built from the stream
+    for k in (3, 4, 7):
+        g = I.cycle(k)
+        s, rsum = 0, 0
+        for _ in range(k):
+            out, s = oracle.splitmix64_next(s)
+            rsum += out
+        expect = _splitmix_draw((rsum + (k - 1) * GAMMA) & MASK)
+        assert oracle.enumerate_cycles(g).hash == expect
+        assert oracle.bruteforce(g).hash == expect
+
+
 # ------------------------------------------------------------------ degree labelling
 
 def _golden_labelings():
@@ -234,6 +275,44 @@ def test_named_small_graphs_equal_definition():
         a = oracle.enumerate_cycles(g, cycles=True)
         b = oracle.bruteforce(g, cycles=True)
         assert sorted(a.cycles) == sorted(b.cycles) and a.hash == b.hash
+
+
+def _check_canonical_order(g, cycles):
+    """Canonical ordered form (cycle lists): the smallest id first, then towards the
+    smaller of its two cycle neighbours; consecutive entries (and last-first) are edges."""
+    edges = {(int(a), int(b)) for a, b in g.edges().tolist()}
+    edges |= {(b, a) for a, b in edges}
+    for c in cycles:
+        k = len(c)
+        assert k >= 3
+        assert c[0] == min(c), c
+        assert c[1] < c[-1], c
+        assert len(set(c)) == k, c
+        for i in range(k):
+            assert (c[i], c[(i + 1) % k]) in edges, c
+
+
+@pytest.mark.parametrize("chunk", range(3))
+def test_cycle_lists_in_canonical_order(chunk):
+    graphs = _small_graphs(40, 3000 + 100 * chunk)
+    if chunk == 0:
+        graphs += [I.grid(3, 4), I.grid(4, 4), I.complete_bipartite(3, 4), I.wheel(7), I.complete(6),
+                   I.cycle(9), I.grid(2, 9), I.complete_bipartite(2, 8)]
+    for g in graphs:
+        _check_canonical_order(g, oracle.enumerate_cycles(g, cycles=True).cycles)
+        _check_canonical_order(g, oracle.bruteforce(g, cycles=True).cycles)
+
+
+def test_canonical_order_worked_examples():
+    # worked by hand: the 6-cycle 0-1-2-3-4-5 renamed so that the smallest id (1) sits
+    # in the middle of the input order and its smaller neighbour lies "backwards"
+    g = I.from_edges(8, [(7, 4), (4, 1), (1, 6), (6, 2), (2, 5), (5, 7)])
+    assert oracle.enumerate_cycles(g, cycles=True).cycles == [(1, 4, 7, 5, 2, 6)]
+    assert oracle.bruteforce(g, cycles=True).cycles == [(1, 4, 7, 5, 2, 6)]
+    # the 4-cycle 3-0-2-1: 0's neighbours are 3 and 2, so 0, 2, 1, 3
+    g = I.from_edges(4, [(3, 0), (0, 2), (2, 1), (1, 3)])
+    assert oracle.enumerate_cycles(g, cycles=True).cycles == [(0, 2, 1, 3)]
+    assert oracle.bruteforce(g, cycles=True).cycles == [(0, 2, 1, 3)]
 
 
 def test_networkx_enumerator():
