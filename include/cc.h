@@ -201,6 +201,23 @@ cc_status cc_enumerate(cc_graph* g, uint32_t max_len, uint64_t* out_hist, uint64
                        uint64_t* out_tcount, cc_cycles* out_cycles, cc_run_info* out_info);
 
 /*
+ * One part of an enumeration split over its initial triplets, for several GPUs (or several
+ * calls).  Section 4.3 gives every initial triplet its own work item (Algorithm 2), and each
+ * triplet roots an independent subtree of chordless paths in Algorithm 3, so the subtrees
+ * can be enumerated apart and their results added.  The initial triplet, or triangle,
+ * <x, u, y> (original ids, l(u) < l(x) < l(y)) belongs to part
+ *     mix((u * n + x) * n + y) mod nparts          (mix: the SplitMix64 finaliser above)
+ * which does not depend on the labelling's tie rule or on thread order.  Summing out_hist,
+ * out_hash (mod 2^64) and out_tcount over parts 0 .. nparts-1 gives exactly what
+ * cc_enumerate returns; cycle lists of the parts are disjoint and together hold every
+ * cycle.  nparts = 1 is cc_enumerate.  Arguments and errors as for cc_enumerate, plus
+ * CC_ERR_ARG when nparts == 0 or part >= nparts.
+ */
+cc_status cc_enumerate_part(cc_graph* g, uint32_t max_len, uint32_t part, uint32_t nparts, uint64_t* out_hist,
+                            uint64_t* out_hash, uint64_t* out_tcount, cc_cycles* out_cycles,
+                            cc_run_info* out_info);
+
+/*
  * Streamed cycle lists.  Table 1 of the paper counts the 71.5 M cycles of the 8 x 10 grid
  * without storing them, and Section 6 leaves a transport between host and GPU memory to
  * future work; this call lists every cycle of any size of output through bounded device
@@ -309,6 +326,29 @@ cc_status cc_batch_submit(cc_context* ctx, uint32_t count, const uint32_t* n,
                           cc_batch_id* out_batch);
 
 /*
+ * Device-resident batches (the same work as cc_batch_submit, split so that repeated runs
+ * over one set of graphs copy nothing to the device).  cc_batch_load validates and copies
+ * `count` graphs (arguments as for cc_batch_submit) into device memory owned by the set
+ * and returns when the copies are done (the caller may free its arrays).  cc_batch_run
+ * enumerates every graph of the set with at most max_len vertices per cycle, like
+ * cc_batch_submit (asynchronous; collect with cc_batch_poll on the set's context; one
+ * batch in flight per context).  cc_batch_free waits for a batch of the set still in
+ * flight (its results are then dropped) and frees the set.  The set belongs to the
+ * context it was loaded on and must be freed before that context is destroyed.
+ * Errors of cc_batch_load: CC_ERR_ARG, CC_ERR_INVALID_GRAPH and CC_ERR_UNSUPPORTED (the
+ * index of the first bad graph in *bad_graph when bad_graph is not NULL), CC_ERR_OOM,
+ * CC_ERR_CUDA.  Errors of cc_batch_run: CC_ERR_ARG (NULL, or a batch already in flight on
+ * the context), CC_ERR_CAPACITY (the initial triplets need more than half the frontier
+ * memory), CC_ERR_OOM, CC_ERR_CUDA.
+ */
+typedef struct cc_batch_set cc_batch_set;
+cc_status cc_batch_load(cc_context* ctx, uint32_t count, const uint32_t* n, const uint64_t* row_off,
+                        const uint32_t* row_ptr, const uint64_t* col_off, const uint32_t* col_idx,
+                        cc_batch_set** out, uint32_t* bad_graph);
+cc_status cc_batch_run(cc_batch_set* set, uint32_t max_len, cc_batch_id* out_batch);
+void cc_batch_free(cc_batch_set* set);
+
+/*
  * Wait up to timeout_us microseconds for a batch.  CC_PENDING if it is still running
  * (call again), otherwise its final status; on CC_OK the outputs are filled:
  *   hist        count * hist_stride entries; graph g's histogram at hist[g * hist_stride],
@@ -317,7 +357,10 @@ cc_status cc_batch_submit(cc_context* ctx, uint32_t count, const uint32_t* n,
  *   paths       count entries (stored paths per graph), or NULL
  *   done_us     count entries: microseconds from the start of the batch's expansion until
  *               the step that finished the graph's last path, or NULL
- *   info        whole-batch timings, or NULL
+ *   info        whole-batch timings, or NULL: ms_proc = device time of labelling, seeding
+ *               and expansion (from the start of the batch's device work; the input copies
+ *               of cc_batch_submit are not included), ms_engine = the expansion launch,
+ *               ms_total = ms_proc plus the result copies of this call
  */
 cc_status cc_batch_poll(cc_context* ctx, cc_batch_id batch, uint32_t timeout_us, uint64_t* hist,
                         uint32_t hist_stride, uint64_t* hash, uint64_t* paths, double* done_us,
@@ -401,9 +444,12 @@ uint64_t cc_serve_predict_bytes(uint32_t n, uint64_t m, uint32_t max_degree);
  *                        after the stream has finished its work
  *   out_hist, out_hash, out_tcount   host outputs as for cc_enumerate (out_tcount may be NULL)
  * Errors: CC_ERR_UNSUPPORTED if n > CC_NOALLOC_MAX_N, CC_ERR_CAPACITY if the initial triplets
- * cannot fit the array, CC_ERR_ARG, CC_ERR_CUDA, CC_ERR_TIMEOUT.
+ * cannot fit the array, CC_ERR_INVALID_GRAPH (also for row_ptr[n] > n (n - 1), checked before
+ * col_idx is read), CC_ERR_ARG, CC_ERR_CUDA, CC_ERR_TIMEOUT.
  * The array's device address is looked up (cudaGetSymbolAddress) on the first call on each
- * device, so make that first call before any stream capture.  All calls share the array and
+ * device, so make that first call before any stream capture.  That address lasts as long
+ * as the device's primary context: after a cudaDeviceReset (or any other reset of that
+ * context) the array may move, so do not call this function on a device that was reset.  All calls share the array and
  * each call clears the parts that must start at zero; calls whose GPU work overlaps (other
  * streams or host threads) race on it and must be serialised by the caller.
  */

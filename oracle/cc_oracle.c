@@ -136,10 +136,18 @@ static int pool_reserve(pool_t* p, uint64_t extra) {
  * Algorithm 1.  Returns 0, or -1 on allocation failure.
  *   hist[0..L']       out: per-length cycle counts (caller zeroes nothing; we zero it)
  *   tcount[0..L']     out (optional): tcount[t] = number of paths of t vertices placed in T
- *   part, nparts      process only the triplets whose index in generation order is
- *                     congruent to part modulo nparts (triangles are counted by part 0);
- *                     nparts = 1 runs the whole algorithm.
+ *   part, nparts      process only the initial triplets and triangles <x,u,y> of this
+ *                     part: mix((u * n + x) * n + y) mod nparts == part, original ids (the
+ *                     library's split of T(G); every triplet roots its own subtree, Section
+ *                     4.3, so the parts add up to the whole); nparts = 1 runs everything.
  */
+/* The part of the initial triplet or triangle <x,u,y>: mix((u n + x) n + y) mod nparts. */
+static int in_part(uint32_t x, uint32_t u, uint32_t y, uint32_t n, uint32_t part, uint32_t nparts) {
+  if (nparts <= 1) return 1;
+  uint64_t key = ((uint64_t)u * n + x) * n + y;
+  return mix(key) % nparts == part;
+}
+
 int cco_enumerate(uint32_t n, const uint32_t* row_ptr, const uint32_t* col, uint32_t max_len,
                   uint32_t part, uint32_t nparts,
                   uint64_t* hist, uint64_t* hash, uint64_t* tcount,
@@ -181,18 +189,17 @@ int cco_enumerate(uint32_t n, const uint32_t* row_ptr, const uint32_t* col, uint
   if (L >= 3) {
     /* Algorithm 1, initial sets: triplets <x,u,y> with x,y in Adj(u) and l(u) < l(x) < l(y);
      * (x,y) in E gives a triangle (cycle), otherwise an initial chordless path. */
-    uint64_t triplet_index = 0;
     for (uint32_t u = 0; u < n; ++u)
       for (uint32_t a = row_ptr[u]; a < row_ptr[u + 1]; ++a)
         for (uint32_t b = row_ptr[u]; b < row_ptr[u + 1]; ++b) {
           uint32_t x = col[a], y = col[b];
           if (!(label[u] < label[x] && label[x] < label[y])) continue;
+          if (!in_part(x, u, y, n, part, nparts)) continue;
           uint32_t c[3] = {x, u, y};
           if (adjacent(row_ptr, col, x, y)) {
-            if (part == 0) emit_cycle(&s, c, 3);
+            emit_cycle(&s, c, 3);
           } else if (L > 3) {
-            if (triplet_index % nparts == part) { PUSH_PATH(c, 3, y); }
-            triplet_index += 1;
+            PUSH_PATH(c, 3, y);
           }
         }
   }

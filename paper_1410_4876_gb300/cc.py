@@ -131,8 +131,15 @@ SIGNATURES = {
     "cc_graph_info": (ctypes.c_int32, [ctypes.c_void_p, _u32p, _u64p, _u32p]),
     "cc_enumerate": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_uint32, _u64p, _u64p, _u64p,
                                       ctypes.POINTER(cc_cycles), ctypes.POINTER(cc_run_info)]),
+    "cc_enumerate_part": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32,
+                                           _u64p, _u64p, _u64p, ctypes.POINTER(cc_cycles),
+                                           ctypes.POINTER(cc_run_info)]),
     "cc_batch_submit": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_uint32, _u32p, _u64p, _u32p, _u64p, _u32p,
                                          ctypes.c_uint32, _u64p]),
+    "cc_batch_load": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_uint32, _u32p, _u64p, _u32p, _u64p, _u32p,
+                                       ctypes.POINTER(ctypes.c_void_p), _u32p]),
+    "cc_batch_run": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_uint32, _u64p]),
+    "cc_batch_free": (None, [ctypes.c_void_p]),
     "cc_batch_poll": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32, _u64p, ctypes.c_uint32,
                                        _u64p, _u64p, _dblp, ctypes.POINTER(cc_run_info)]),
     "cc_get_trace": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_uint32, _u64p, _u64p, _u64p]),
@@ -243,8 +250,10 @@ def cc_graph_free(g) -> None:
     load_library().cc_graph_free(g)
 
 
-def cc_enumerate(g, n: int, max_len: int = 0, tcount: bool = True, cycles_capacity: Optional[tuple] = None):
-    """Returns (status, hist, hash, tcount, cycles, info); cycles is a list of tuples or None."""
+def cc_enumerate(g, n: int, max_len: int = 0, tcount: bool = True, cycles_capacity: Optional[tuple] = None,
+                 part: int = 0, nparts: int = 1):
+    """Returns (status, hist, hash, tcount, cycles, info); cycles is a list of tuples or None.
+    nparts > 1 calls cc_enumerate_part (this part of the initial triplets only)."""
     L = n if (max_len == 0 or max_len > n) else max_len
     hist = np.zeros(L + 1, dtype=np.uint64)
     tc = np.zeros(L + 1, dtype=np.uint64) if tcount else None
@@ -257,8 +266,14 @@ def cc_enumerate(g, n: int, max_len: int = 0, tcount: bool = True, cycles_capaci
         offs = np.zeros(cap_c + 1, dtype=np.uint64)
         verts = np.zeros(max(cap_v, 1), dtype=np.uint32)
         cyc = cc_cycles(cap_c, cap_v, _p64(offs), _p32(verts), 0, 0)
-    s = load_library().cc_enumerate(g, max_len, _p64(hist), ctypes.byref(hsh), _p64(tc) if tc is not None else None,
-                                    ctypes.byref(cyc) if cyc is not None else None, ctypes.byref(info))
+    if nparts != 1 or part:
+        s = load_library().cc_enumerate_part(g, max_len, part, nparts, _p64(hist), ctypes.byref(hsh),
+                                             _p64(tc) if tc is not None else None,
+                                             ctypes.byref(cyc) if cyc is not None else None, ctypes.byref(info))
+    else:
+        s = load_library().cc_enumerate(g, max_len, _p64(hist), ctypes.byref(hsh),
+                                        _p64(tc) if tc is not None else None,
+                                        ctypes.byref(cyc) if cyc is not None else None, ctypes.byref(info))
     out_cycles = None
     if cyc is not None:
         if s == CC_OK:
@@ -312,6 +327,29 @@ def cc_batch_submit(ctx, graphs: Sequence, max_len: int = 0):
     s = load_library().cc_batch_submit(ctx, len(graphs), _p32(ns), _p64(row_off), _p32(rp), _p64(col_off), _p32(cl),
                                        max_len, ctypes.byref(bid))
     return s, int(bid.value)
+
+
+def cc_batch_load(ctx, packed):
+    """packed = (n, row_off, row_ptr, col_off, col_idx) as made by inputs.pack; returns
+    (status, set handle, index of the first bad graph)."""
+    ns, row_off, rp, col_off, cl = packed
+    if cl.size == 0:
+        cl = np.zeros(1, dtype=np.uint32)
+    h = ctypes.c_void_p(None)
+    bad = ctypes.c_uint32(0)
+    s = load_library().cc_batch_load(ctx, ns.size, _p32(ns), _p64(row_off), _p32(rp), _p64(col_off), _p32(cl),
+                                     ctypes.byref(h), ctypes.byref(bad))
+    return s, h.value, int(bad.value)
+
+
+def cc_batch_run(bset, max_len: int = 0):
+    bid = ctypes.c_uint64(0)
+    s = load_library().cc_batch_run(bset, max_len, ctypes.byref(bid))
+    return s, int(bid.value)
+
+
+def cc_batch_free(bset) -> None:
+    load_library().cc_batch_free(bset)
 
 
 def cc_batch_poll(ctx, batch: int, count: int, timeout_us: int = 0, hist_stride: int = 65):
@@ -411,26 +449,62 @@ class Context:
         done_us[count], info)."""
         s, bid = cc_batch_submit(self.handle, graphs, max_len)
         _check(s, "cc_batch_submit")
-        import time
-        t_end = time.time() + timeout_s
-        while True:
-            s, hist, hsh, paths, done, info = cc_batch_poll(self.handle, bid, len(graphs), 200000)
-            if s != CC_PENDING:
-                break
-            if time.time() > t_end:
-                raise CCError(CC_ERR_TIMEOUT, "cc_batch_poll")
-        _check(s, "cc_batch_poll")
-        return hist, hsh, paths, done, info
+        return _wait_batch(self, bid, len(graphs), timeout_s)
+
+
+    def load_batch(self, graphs: Sequence) -> "BatchSet":
+        from .inputs import pack
+        s, h, bad = cc_batch_load(self.handle, pack(graphs))
+        _check(s, f"cc_batch_load (graph {bad})")
+        return BatchSet(self, h, len(graphs))
+
+
+def _wait_batch(ctx: "Context", bid: int, count: int, timeout_s: float):
+    import time
+    t_end = time.time() + timeout_s
+    while True:
+        s, hist, hsh, paths, done, info = cc_batch_poll(ctx.handle, bid, count, 200000)
+        if s != CC_PENDING:
+            break
+        if time.time() > t_end:
+            raise CCError(CC_ERR_TIMEOUT, "cc_batch_poll")
+    _check(s, "cc_batch_poll")
+    return hist, hsh, paths, done, info
+
+
+class BatchSet:
+    """Graphs resident on the device for repeated batched enumeration (cc_batch_load)."""
+
+    def __init__(self, ctx: Context, handle, count: int):
+        self.ctx, self.handle, self.count = ctx, handle, count
+
+    def run(self, max_len: int = 0, timeout_s: float = 600.0):
+        """cc_batch_run + cc_batch_poll: (hist[count, 65], hash[count], paths[count],
+        done_us[count], info)."""
+        s, bid = cc_batch_run(self.handle, max_len)
+        _check(s, "cc_batch_run")
+        return _wait_batch(self.ctx, bid, self.count, timeout_s)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            cc_batch_free(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
 
 
 class LoadedGraph:
     def __init__(self, ctx: Context, handle, n: int):
         self.ctx, self.handle, self.n = ctx, handle, n
 
-    def enumerate(self, max_len: int = 0, cycles: bool = False) -> Result:
+    def enumerate(self, max_len: int = 0, cycles: bool = False, part: int = 0, nparts: int = 1) -> Result:
         cap = (1024, 8192) if cycles else None
         while True:
-            s, hist, h, tc, cyc, info = cc_enumerate(self.handle, self.n, max_len, True, cap)
+            s, hist, h, tc, cyc, info = cc_enumerate(self.handle, self.n, max_len, True, cap, part, nparts)
             if cycles and s == CC_ERR_TRUNCATED:
                 cap = (int(cyc[0]) + 16, int(cyc[1]) + 64)
                 continue

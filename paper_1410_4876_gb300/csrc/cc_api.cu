@@ -60,6 +60,7 @@ extern "C" cc_status cc_context_create(const cc_options* opts, cc_context** out)
   if (dev_alloc(c, (void**)&c->ctl, sizeof(Control)) != CC_OK ||
       cudaMallocHost((void**)&c->h_ctl, sizeof(Control)) != cudaSuccess ||
       cudaEventCreate(&c->ev0) != cudaSuccess || cudaEventCreate(&c->ev1) != cudaSuccess ||
+      cudaEventCreate(&c->ev4) != cudaSuccess ||
       cudaEventCreate(&c->ev2) != cudaSuccess || cudaEventCreate(&c->ev3) != cudaSuccess) {
     (void)cudaGetLastError();
     cc_context_destroy(c);
@@ -86,6 +87,10 @@ extern "C" void cc_context_destroy(cc_context* c) {
   if (c->stream) cudaStreamSynchronize(c->stream);
   auto& b = c->batch;
   dev_free(c, b.d_pack);
+  if (b.own) {
+    dev_free(c, b.own->d_in);
+    delete b.own;
+  }
   dev_free(c, c->d_res);
   dev_free(c, c->d_trace);
   dev_free(c, c->frames);
@@ -99,6 +104,7 @@ extern "C" void cc_context_destroy(cc_context* c) {
   if (c->ev1) cudaEventDestroy(c->ev1);
   if (c->ev2) cudaEventDestroy(c->ev2);
   if (c->ev3) cudaEventDestroy(c->ev3);
+  if (c->ev4) cudaEventDestroy(c->ev4);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
   (void)cudaGetLastError();
   delete c;
@@ -215,8 +221,10 @@ struct StreamOut {
 };
 
 cc_status enumerate_impl(cc_graph* g, uint32_t max_len, uint64_t* out_hist, uint64_t* out_hash, uint64_t* out_tcount,
-                         cc_cycles* out_cycles, StreamOut* so, cc_run_info* out_info) {
+                         cc_cycles* out_cycles, StreamOut* so, cc_run_info* out_info, uint32_t part = 0,
+                         uint32_t nparts = 1) {
   if (!g || !out_hist || !out_hash) return CC_ERR_ARG;
+  if (nparts == 0 || part >= nparts) return CC_ERR_ARG;
   if (out_cycles && ((out_cycles->capacity_cycles && !out_cycles->offsets) ||
                      (out_cycles->capacity_vertices && !out_cycles->vertices)))
     return CC_ERR_ARG;
@@ -311,6 +319,8 @@ cc_status enumerate_impl(cc_graph* g, uint32_t max_len, uint64_t* out_hist, uint
   p.pf = c->opts.paths_per_thread;
   p.fuse_ok = (!is_csr(kind) && !(c->opts.flags & CC_FLAG_NO_FUSE)) ? 1u : 0u;
   p.seed_entries = (unsigned int)(2 * g->m);
+  p.part = part;
+  p.nparts = nparts;
   if (!c->d_trace) {
     if ((s = dev_alloc(c, (void**)&c->d_trace, 16ull * kTraceCap))) {
       free_cyc();
@@ -576,6 +586,12 @@ extern "C" cc_status cc_enumerate(cc_graph* g, uint32_t max_len, uint64_t* out_h
   return enumerate_impl(g, max_len, out_hist, out_hash, out_tcount, out_cycles, nullptr, out_info);
 }
 
+extern "C" cc_status cc_enumerate_part(cc_graph* g, uint32_t max_len, uint32_t part, uint32_t nparts,
+                                       uint64_t* out_hist, uint64_t* out_hash, uint64_t* out_tcount,
+                                       cc_cycles* out_cycles, cc_run_info* out_info) {
+  return enumerate_impl(g, max_len, out_hist, out_hash, out_tcount, out_cycles, nullptr, out_info, part, nparts);
+}
+
 extern "C" cc_status cc_enumerate_stream(cc_graph* g, uint32_t max_len, uint64_t chunk_cycles,
                                          uint64_t chunk_vertices, cc_cycle_sink sink, void* user, uint64_t* out_hist,
                                          uint64_t* out_hash, uint64_t* out_tcount, uint32_t* out_rounds,
@@ -606,55 +622,130 @@ extern "C" cc_status cc_get_trace(cc_context* c, uint32_t cap, uint64_t* t_ns, u
 
 // ------------------------------------------------------------------ batch
 
-extern "C" cc_status cc_batch_submit(cc_context* c, uint32_t count, const uint32_t* n, const uint64_t* row_off,
-                                     const uint32_t* row_ptr, const uint64_t* col_off, const uint32_t* col_idx,
-                                     uint32_t max_len, cc_batch_id* out) {
-  if (!c || !out || !n || !row_off || !row_ptr || !col_off) return CC_ERR_ARG;
-  if (c->batch.active) return CC_ERR_ARG;
-  if (count == 0 || count > kMultiMaxSlots) return count ? CC_ERR_UNSUPPORTED : CC_ERR_ARG;
-  auto& b = c->batch;
-  // validate every graph and build the packed, sorted copy
-  std::vector<uint32_t> rows, cols;
+// Validate and pack `count` graphs, and copy them into the set's device buffer (grown on
+// demand).  Returns with the copies finished, so the caller's arrays may be released.
+static cc_status batch_load_into(cc_batch_set* bs, uint32_t count, const uint32_t* n, const uint64_t* row_off,
+                                 const uint32_t* row_ptr, const uint64_t* col_off, const uint32_t* col_idx,
+                                 uint32_t* bad) {
+  cc_context* c = bs->ctx;
+  if (!n || !row_off || !row_ptr || !col_off) return CC_ERR_ARG;
+  if (count == 0) return CC_ERR_ARG;
+  if (count > kMultiMaxSlots) return CC_ERR_UNSUPPORTED;
+  std::vector<uint32_t> rows, cols, sorted;
   std::vector<unsigned long long> roff(count + 1), coff(count + 1);
-  std::vector<unsigned int> L(count);
   unsigned long long tb_total = 0;
   unsigned int maxch = 1;
-  std::vector<uint32_t> sorted;
   for (uint32_t g = 0; g < count; ++g) {
     if (n[g] > kMultiMaxN) {
-      *out = g;
+      *bad = g;
       return CC_ERR_UNSUPPORTED;
     }
     const uint32_t* rp = row_ptr + row_off[g];
     unsigned int md = 0;
     cc_status s = validate_csr(n[g], rp, col_idx ? col_idx + col_off[g] : nullptr, sorted, &md);
     if (s) {
-      *out = g;
+      *bad = g;
       return s;
     }
     roff[g] = rows.size();
     coff[g] = cols.size();
     rows.insert(rows.end(), rp, rp + n[g] + 1);
     cols.insert(cols.end(), sorted.begin(), sorted.end());
-    L[g] = (max_len == 0 || max_len > n[g]) ? n[g] : max_len;
     const unsigned long long m = rp[n[g]] / 2;
+    // |T(G)| <= (max degree - 1) m / 2 (Section 2): the seed region's bound
     if (md > 1) tb_total += (unsigned long long)(md - 1) * m / 2;
     maxch = std::max(maxch, md > 1 ? md - 1 : 1u);
   }
   roff[count] = rows.size();
   coff[count] = cols.size();
+  auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
+  size_t off = 0;
+  bs->o_rows = off; off = al(off + 4 * rows.size());
+  bs->o_cols = off; off = al(off + 4 * std::max<size_t>(cols.size(), 1));
+  bs->o_roff = off; off = al(off + 8 * (count + 1));
+  bs->o_coff = off; off = al(off + 8 * (count + 1));
+  bs->o_n = off; off = al(off + 4 * count);
+  const size_t total = off;
+  cc_status s;
+  if (bs->d_in_bytes < total) {
+    dev_free(c, bs->d_in);
+    bs->d_in = nullptr;
+    bs->d_in_bytes = 0;
+    if ((s = dev_alloc(c, &bs->d_in, total))) return s;
+    bs->d_in_bytes = total;
+  }
+  unsigned char* base = static_cast<unsigned char*>(bs->d_in);
+  cudaStream_t st = c->stream;
+  cudaError_t e = cudaSuccess;
+  auto ok = [&](cudaError_t x) {
+    if (e == cudaSuccess && x != cudaSuccess) e = x;
+  };
+  ok(cudaMemcpyAsync(base + bs->o_rows, rows.data(), 4 * rows.size(), cudaMemcpyHostToDevice, st));
+  if (!cols.empty()) ok(cudaMemcpyAsync(base + bs->o_cols, cols.data(), 4 * cols.size(), cudaMemcpyHostToDevice, st));
+  ok(cudaMemcpyAsync(base + bs->o_roff, roff.data(), 8 * (count + 1), cudaMemcpyHostToDevice, st));
+  ok(cudaMemcpyAsync(base + bs->o_coff, coff.data(), 8 * (count + 1), cudaMemcpyHostToDevice, st));
+  ok(cudaMemcpyAsync(base + bs->o_n, n, 4 * count, cudaMemcpyHostToDevice, st));
+  // synchronise so the host copies can be released when this call returns
+  ok(cudaStreamSynchronize(st));
+  if (e != cudaSuccess) {
+    (void)cudaGetLastError();
+    return cuda_status(e);
+  }
+  bs->count = count;
+  bs->n.assign(n, n + count);
+  bs->tb_total = tb_total;
+  bs->maxch = maxch;
+  bs->h2d_bytes = 4 * rows.size() + 4 * cols.size() + 16ull * (count + 1) + 4ull * count;
+  return CC_OK;
+}
+
+extern "C" cc_status cc_batch_load(cc_context* c, uint32_t count, const uint32_t* n, const uint64_t* row_off,
+                                   const uint32_t* row_ptr, const uint64_t* col_off, const uint32_t* col_idx,
+                                   cc_batch_set** out, uint32_t* bad_graph) {
+  if (!c || !out) return CC_ERR_ARG;
+  *out = nullptr;
+  cc_batch_set* bs = new (std::nothrow) cc_batch_set;
+  if (!bs) return CC_ERR_OOM;
+  bs->ctx = c;
+  uint32_t bad = 0;
+  cc_status s = batch_load_into(bs, count, n, row_off, row_ptr, col_off, col_idx, &bad);
+  if (s) {
+    if (bad_graph) *bad_graph = bad;
+    dev_free(c, bs->d_in);
+    delete bs;
+    return s;
+  }
+  *out = bs;
+  return CC_OK;
+}
+
+extern "C" void cc_batch_free(cc_batch_set* bs) {
+  if (!bs) return;
+  cc_context* c = bs->ctx;
+  // a batch of this set may still be running: free after the context's stream
+  if (c->batch.active && c->batch.set == bs) {
+    cudaStreamSynchronize(c->stream);
+    c->batch.active = false;
+  }
+  dev_free(c, bs->d_in);
+  (void)cudaGetLastError();
+  delete bs;
+}
+
+// Labelling, seeding and one persistent expansion launch for every graph of a loaded set
+// (asynchronous on the context's stream; cc_batch_poll collects the results).
+static cc_status batch_run(cc_batch_set* bs, uint32_t max_len, cc_batch_id* out) {
+  cc_context* c = bs->ctx;
+  auto& b = c->batch;
+  if (b.active) return CC_ERR_ARG;
+  const unsigned int count = bs->count;
   cc_status s;
   if ((s = ensure_arena(c))) return s;
   if ((s = ensure_frames(c, 70))) return s;
-  // device pack: rows | cols | roff | coff | n | adj | rtab | Lg | hist | hash | tcount | last | ts
+  // work pack: adj | rtab | Lg | hist | hash | tcount | last | ts
   b.ts_cap = 1u << 16;
   auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
   size_t off = 0;
-  const size_t o_rows = off; off = al(off + 4 * rows.size());
-  const size_t o_cols = off; off = al(off + 4 * std::max<size_t>(cols.size(), 1));
-  const size_t o_roff = off; off = al(off + 8 * (count + 1));
-  const size_t o_coff = off; off = al(off + 8 * (count + 1));
-  const size_t o_n = off; off = al(off + 4 * count);
   const size_t o_adj = off; off = al(off + 8ull * 64 * count);
   const size_t o_rtab = off; off = al(off + 8ull * 64 * count);
   const size_t o_Lg = off; off = al(off + count);
@@ -672,26 +763,12 @@ extern "C" cc_status cc_batch_submit(cc_context* c, uint32_t count, const uint32
     b.d_pack_bytes = total;
   }
   unsigned char* base = static_cast<unsigned char*>(b.d_pack);
+  unsigned char* in = static_cast<unsigned char*>(bs->d_in);
   cudaStream_t st = c->stream;
   cudaError_t e = cudaSuccess;
   auto ok = [&](cudaError_t x) {
     if (e == cudaSuccess && x != cudaSuccess) e = x;
   };
-  std::vector<unsigned int> nv(n, n + count);
-  ok(cudaEventRecord(c->ev0, st));
-  ok(cudaMemcpyAsync(base + o_rows, rows.data(), 4 * rows.size(), cudaMemcpyHostToDevice, st));
-  if (!cols.empty()) ok(cudaMemcpyAsync(base + o_cols, cols.data(), 4 * cols.size(), cudaMemcpyHostToDevice, st));
-  ok(cudaMemcpyAsync(base + o_roff, roff.data(), 8 * (count + 1), cudaMemcpyHostToDevice, st));
-  ok(cudaMemcpyAsync(base + o_coff, coff.data(), 8 * (count + 1), cudaMemcpyHostToDevice, st));
-  ok(cudaMemcpyAsync(base + o_n, nv.data(), 4 * count, cudaMemcpyHostToDevice, st));
-  ok(cudaMemsetAsync(base + o_hist, 0, o_ts - o_hist, st));
-  ok(cudaMemsetAsync(c->ctl, 0, sizeof(Control), st));
-  // synchronise so the host copies can be released when this call returns
-  ok(cudaStreamSynchronize(st));
-  if (e != cudaSuccess) {
-    (void)cudaGetLastError();
-    return cuda_status(e);
-  }
   EngineParams p{};
   p.arena = c->arena;
   p.arena_bytes = c->arena_bytes;
@@ -700,7 +777,7 @@ extern "C" cc_status cc_batch_submit(cc_context* c, uint32_t count, const uint32
   p.max_depth = c->frames_cap;
   p.n = 64;
   p.L = 64;
-  p.maxch = maxch;
+  p.maxch = bs->maxch;
   p.adj = reinterpret_cast<unsigned long long*>(base + o_adj);
   p.rtab = reinterpret_cast<unsigned long long*>(base + o_rtab);
   p.Lg = base + o_Lg;
@@ -713,7 +790,8 @@ extern "C" cc_status cc_batch_submit(cc_context* c, uint32_t count, const uint32
   p.spin_limit = c->opts.spin_limit ? c->opts.spin_limit : kDefaultSpin;
   p.fresh = 1;
   p.pf = c->opts.paths_per_thread;
-  const unsigned long long seed_stride = round_up(tb_total + 8, 8);
+  p.fuse_ok = (c->opts.flags & CC_FLAG_NO_FUSE) ? 0u : 1u;
+  const unsigned long long seed_stride = round_up(bs->tb_total + 8, 8);
   const unsigned long long seed_bytes = bitset_region_bytes(seed_stride, 1);
   if (seed_bytes > c->arena_bytes / 2) return CC_ERR_CAPACITY;
   p.seed_stride = seed_stride;
@@ -721,12 +799,15 @@ extern "C" cc_status cc_batch_submit(cc_context* c, uint32_t count, const uint32
   const int block = c->opts.threads_per_block ? (int)c->opts.threads_per_block : 256;
   const int grid = engine_grid(c, Kind::Multi, block, 0);
   if (grid <= 0) return CC_ERR_CUDA;
-  ok(launch_label_seed_multi(reinterpret_cast<unsigned int*>(base + o_rows),
-                             reinterpret_cast<unsigned long long*>(base + o_roff),
-                             reinterpret_cast<unsigned int*>(base + o_cols),
-                             reinterpret_cast<unsigned long long*>(base + o_coff),
-                             reinterpret_cast<unsigned int*>(base + o_n), nullptr, count, 0, max_len, p, 0, seed_stride,
-                             &c->ctl->seed_count, &c->ctl->seed_next, st));
+  ok(cudaEventRecord(c->ev0, st));
+  ok(cudaMemsetAsync(base + o_hist, 0, o_ts - o_hist, st));
+  ok(cudaMemsetAsync(c->ctl, 0, sizeof(Control), st));
+  ok(launch_label_seed_multi(reinterpret_cast<unsigned int*>(in + bs->o_rows),
+                             reinterpret_cast<unsigned long long*>(in + bs->o_roff),
+                             reinterpret_cast<unsigned int*>(in + bs->o_cols),
+                             reinterpret_cast<unsigned long long*>(in + bs->o_coff),
+                             reinterpret_cast<unsigned int*>(in + bs->o_n), nullptr, count, 0, max_len, p, 0,
+                             seed_stride, &c->ctl->seed_count, &c->ctl->seed_next, st));
   ok(cudaEventRecord(c->ev1, st));
   ok(launch_engine(Kind::Multi, p, grid, block, 0, st));
   ok(cudaEventRecord(c->ev2, st));
@@ -735,9 +816,12 @@ extern "C" cc_status cc_batch_submit(cc_context* c, uint32_t count, const uint32
     return cuda_status(e);
   }
   b.active = true;
+  b.set = bs;
   b.count = count;
   b.max_len = max_len;
-  b.L = L;
+  b.L.resize(count);
+  for (unsigned int g = 0; g < count; ++g)
+    b.L[g] = (max_len == 0 || max_len > bs->n[g]) ? bs->n[g] : max_len;
   b.d_hist = p.hist;
   b.d_hash = p.hash;
   b.d_tcount = p.tcount;
@@ -747,6 +831,30 @@ extern "C" cc_status cc_batch_submit(cc_context* c, uint32_t count, const uint32
   b.id = c->next_batch++;
   *out = b.id;
   return CC_OK;
+}
+
+extern "C" cc_status cc_batch_run(cc_batch_set* bs, uint32_t max_len, cc_batch_id* out) {
+  if (!bs || !out) return CC_ERR_ARG;
+  return batch_run(bs, max_len, out);
+}
+
+extern "C" cc_status cc_batch_submit(cc_context* c, uint32_t count, const uint32_t* n, const uint64_t* row_off,
+                                     const uint32_t* row_ptr, const uint64_t* col_off, const uint32_t* col_idx,
+                                     uint32_t max_len, cc_batch_id* out) {
+  if (!c || !out) return CC_ERR_ARG;
+  if (c->batch.active) return CC_ERR_ARG;
+  if (!c->batch.own) {
+    c->batch.own = new (std::nothrow) cc_batch_set;
+    if (!c->batch.own) return CC_ERR_OOM;
+    c->batch.own->ctx = c;
+  }
+  uint32_t bad = 0;
+  cc_status s = batch_load_into(c->batch.own, count, n, row_off, row_ptr, col_off, col_idx, &bad);
+  if (s) {
+    if (s == CC_ERR_INVALID_GRAPH || s == CC_ERR_UNSUPPORTED) *out = bad;
+    return s;
+  }
+  return batch_run(c->batch.own, max_len, out);
 }
 
 extern "C" cc_status cc_batch_poll(cc_context* c, cc_batch_id id, uint32_t timeout_us, uint64_t* hist,
@@ -777,11 +885,13 @@ extern "C" cc_status cc_batch_poll(cc_context* c, cc_batch_id id, uint32_t timeo
   auto ok = [&](cudaError_t x) {
     if (e == cudaSuccess && x != cudaSuccess) e = x;
   };
+  ok(cudaEventRecord(c->ev3, st));  // result copies: ms_total - ms_proc
   ok(cudaMemcpyAsync(hh.data(), b.d_hist, 8 * hh.size(), cudaMemcpyDeviceToHost, st));
   ok(cudaMemcpyAsync(ht.data(), b.d_tcount, 8 * ht.size(), cudaMemcpyDeviceToHost, st));
   ok(cudaMemcpyAsync(hs.data(), b.d_hash, 8 * count, cudaMemcpyDeviceToHost, st));
   ok(cudaMemcpyAsync(hl.data(), b.d_last, 4 * count, cudaMemcpyDeviceToHost, st));
   ok(cudaMemcpyAsync(c->h_ctl, c->ctl, sizeof(Control), cudaMemcpyDeviceToHost, st));
+  ok(cudaEventRecord(c->ev4, st));
   ok(cudaStreamSynchronize(st));
   if (e != cudaSuccess) {
     (void)cudaGetLastError();
@@ -804,8 +914,11 @@ extern "C" cc_status cc_batch_poll(cc_context* c, cc_batch_id id, uint32_t timeo
   float ms_eng = 0;
   cudaEventElapsedTime(&ms_eng, c->ev1, c->ev2);
   (void)cudaGetLastError();  // a failed timing query leaves no error for the caller
+  float ms_copy = 0;
+  cudaEventElapsedTime(&ms_copy, c->ev3, c->ev4);
+  (void)cudaGetLastError();
   ri.ms_proc = ms_all;
-  ri.ms_total = ms_all;
+  ri.ms_total = ms_all + ms_copy;
   ri.ms_engine = ms_eng;
   ri.steps = nsteps;
   ri.spilled = h.spilled;

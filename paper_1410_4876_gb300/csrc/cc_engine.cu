@@ -22,6 +22,9 @@
 // process_csr_last / process_csr_long_warp (CSR adjacency).
 #include <cooperative_groups.h>
 #include <cstddef>
+#include <mutex>
+#include <utility>
+#include <vector>
 
 #include "cc_internal.cuh"
 
@@ -2158,16 +2161,37 @@ static const void* small_engine_fn(Kind k) {
   }
 }
 
+// The dynamic shared memory limit of a kernel is only ever raised.  A captured CUDA graph
+// keeps each kernel node's shared memory size but not the function attribute, so lowering
+// the attribute for a later launch of a smaller graph would make a replayed node of a
+// larger graph ask for more than its function allows.
+static std::mutex g_smem_mutex;
+static std::vector<std::pair<const void*, size_t>> g_smem_set;
+
+static cudaError_t allow_smem(const void* fn, size_t smem) {
+  std::lock_guard<std::mutex> lock(g_smem_mutex);
+  for (auto& kv : g_smem_set)
+    if (kv.first == fn) {
+      if (kv.second >= smem) return cudaSuccess;
+      const cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e == cudaSuccess) kv.second = smem;
+      return e;
+    }
+  const cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess) g_smem_set.push_back({fn, smem});
+  return e;
+}
+
 cudaError_t engine_occupancy(Kind kind, int block, size_t smem, int* blocks_per_sm) {
   const void* fn = engine_fn(kind);
-  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = allow_smem(fn, smem);
   if (e != cudaSuccess) return e;
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fn, block, smem);
 }
 
 cudaError_t launch_engine(Kind kind, const EngineParams& p, int grid, int block, size_t smem, cudaStream_t st) {
   const void* fn = engine_fn(kind);
-  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = allow_smem(fn, smem);
   if (e != cudaSuccess) return e;
   EngineParams copy = p;
   copy.cluster = 0;
@@ -2181,7 +2205,7 @@ cudaError_t launch_engine(Kind kind, const EngineParams& p, int grid, int block,
 int small_cluster_size(Kind kind, size_t smem) {
   const void* fn = small_engine_fn(kind);
   if (!fn) return 0;
-  if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+  if (allow_smem(fn, smem) != cudaSuccess ||
       cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
     (void)cudaGetLastError();
     return 0;
@@ -2209,8 +2233,7 @@ cudaError_t launch_small_engine(Kind kind, const EngineParams& p, int cluster, s
                                 unsigned long long handover, cudaStream_t st) {
   const void* fn = small_engine_fn(kind);
   if (!fn || cluster <= 0) return cudaErrorInvalidValue;
-  // the attribute is per kernel, and the previous launch may have needed less
-  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = allow_smem(fn, smem);
   if (e != cudaSuccess) return e;
   EngineParams copy = p;
   copy.cluster = 1;

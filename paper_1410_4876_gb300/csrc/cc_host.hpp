@@ -40,7 +40,7 @@ struct cc_context {
   unsigned long long* h_res = nullptr;
   size_t h_res_words = 0;
   Control* h_ctl = nullptr;
-  cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev2 = nullptr, ev3 = nullptr;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev2 = nullptr, ev3 = nullptr, ev4 = nullptr;
   unsigned long long* d_trace = nullptr;  // per-step end time | paths expanded (last call)
   unsigned int trace_cap = 0;
   cc_run_info last{};
@@ -48,14 +48,16 @@ struct cc_context {
   unsigned long long last_t_start = 0;  // globaltimer at the start of the last expansion
   unsigned char* h_stream = nullptr;    // pinned drain buffer of streamed cycle lists
   size_t h_stream_bytes = 0;
-  // batch state
+  // batch state (one batch in flight per context)
   struct Batch {
+    cc_batch_set* set = nullptr;  // the set being enumerated
+    cc_batch_set* own = nullptr;  // the set cc_batch_submit loads into (reused)
     cc_batch_id id = 0;
     bool active = false;
     unsigned int count = 0;
     unsigned int max_len = 0;
     std::vector<unsigned int> L;  // L' per graph
-    void* d_pack = nullptr;       // packed CSR + per-slot tables
+    void* d_pack = nullptr;       // per-slot tables and results
     size_t d_pack_bytes = 0;
     unsigned long long* d_hist = nullptr;
     unsigned long long* d_hash = nullptr;
@@ -67,6 +69,19 @@ struct cc_context {
     int grid = 0;
   } batch;
   cc_batch_id next_batch = 1;
+};
+
+// A set of graphs resident on the device for batched enumeration (cc_batch_load).
+struct cc_batch_set {
+  cc_context* ctx = nullptr;
+  unsigned int count = 0;
+  std::vector<unsigned int> n;     // vertices per graph
+  unsigned long long tb_total = 0; // bound on the initial triplets of all graphs
+  unsigned int maxch = 1;          // bound on children per path (max degree - 1)
+  void* d_in = nullptr;            // rows | cols | row offsets | col offsets | n
+  size_t d_in_bytes = 0;
+  size_t o_rows = 0, o_cols = 0, o_roff = 0, o_coff = 0, o_n = 0;
+  unsigned long long h2d_bytes = 0;  // bytes copied by the last load
 };
 
 struct cc_graph {

@@ -155,7 +155,20 @@ struct EngineParams {
   unsigned int fuse_ok;            // one graph, bitset, persistent grid: two-level steps allowed
   unsigned int cyc_stream;         // CSR cycle list drained between launches: a step takes no
                                    // more paths than the list's room allows, none when it is full
+  unsigned int part, nparts;       // seeding keeps only the initial triplets (and triangles) of
+                                   // this part of nparts (1 = all); see triplet_part
 };
+
+// Triplet sharding: the part of the initial triplet or triangle <x, u, y> (l(u) < l(x) <
+// l(y)) is mix((u n + x) n + y) mod nparts over the ORIGINAL vertex ids, so that the split
+// does not depend on the labelling's tie rule or on the order in which threads find the
+// triplets.  Every triplet roots its own subtree (Section 4.3), so the parts' results add
+// up to the whole.
+__host__ __device__ __forceinline__ unsigned int triplet_part(unsigned int x, unsigned int u, unsigned int y,
+                                                              unsigned int n, unsigned int nparts) {
+  const unsigned long long key = ((unsigned long long)u * n + x) * n + y;
+  return (unsigned int)(mix64(key) % nparts);
+}
 
 #ifdef __CUDACC__
 // Streamed CSR lists: a bound on the cycles that the child <v1 .. vt, v> closes when it is

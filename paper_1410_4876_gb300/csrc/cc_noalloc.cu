@@ -13,10 +13,13 @@
 // Nothing here allocates: no cudaMalloc/cudaFree/cudaMallocAsync, no host heap.  The
 // device address of the array is looked up once per device (cudaGetSymbolAddress, with
 // that device current) on the first call made on that device, so the first call on a
-// device should come before any stream capture.  All calls share the array and it keeps
-// the previous call's contents: everything that must start at zero is cleared by each
-// call, and calls whose work overlaps on the GPU (other streams, other host threads) race
-// on the array and must be serialised by the caller.
+// device should come before any stream capture.  The address stays valid for the life of
+// the device's primary context: a cudaDeviceReset (or any reset of that context) can move
+// the array, and calls after it would use a stale address, so a process that resets a
+// device must not call this entry point on that device afterwards.  All calls share the
+// array and it keeps the previous call's contents: everything that must start at zero is
+// cleared by each call, and calls whose work overlaps on the GPU (other streams, other
+// host threads) race on the array and must be serialised by the caller.
 #include <algorithm>
 #include <cstring>
 #include <mutex>
@@ -40,7 +43,10 @@ constexpr unsigned long long kOffFrames = A256(sizeof(Control));
 constexpr unsigned long long kOffRes = A256(kOffFrames + kMaxFrames * sizeof(Frame));  // hist|tcount|hash
 constexpr unsigned long long kOffRow = A256(kOffRes + 8ull * (2 * (kMaxN + 1) + 1));
 constexpr unsigned long long kOffCol = A256(kOffRow + 4ull * (kMaxN + 1));
-constexpr unsigned long long kOffPerm = A256(kOffCol + 4ull * kMaxN * (kMaxN - 1));
+// the neighbour region holds n (n - 1) ids, the most a simple graph has; check_csr_in_place
+// rejects a row_ptr[n] above that before anything is read or copied
+constexpr unsigned long long kMaxCol = (unsigned long long)kMaxN * (kMaxN - 1);
+constexpr unsigned long long kOffPerm = A256(kOffCol + 4ull * kMaxCol);
 constexpr unsigned long long kOffAdj = A256(kOffPerm + 8ull * kMaxN);
 constexpr unsigned long long kOffRtab = A256(kOffAdj + 8ull * kMaxN * 4);
 constexpr unsigned long long kOffNrow = A256(kOffRtab + 8ull * kMaxN);
@@ -79,12 +85,18 @@ cc_status scratch_for_current_device(unsigned char** out, int* sms) {
 }
 
 // Checks a host CSR in place (sorted strictly increasing rows, ids < n, no self-loops,
-// symmetric), without copying it.
+// symmetric), without copying it.  The offsets are checked first (row_ptr[n] at most
+// n (n - 1), which also bounds the neighbour region of the array, and every row inside
+// [0, row_ptr[n]]), so col_idx is never read beyond row_ptr[n] entries.
 cc_status check_csr_in_place(uint32_t n, const uint32_t* rp, const uint32_t* col, unsigned int* maxdeg) {
   if (rp[0] != 0) return CC_ERR_INVALID_GRAPH;
+  if ((unsigned long long)rp[n] > (unsigned long long)n * (n > 0 ? n - 1 : 0) || rp[n] > kMaxCol)
+    return CC_ERR_INVALID_GRAPH;
+  for (uint32_t v = 0; v < n; ++v)
+    if (rp[v + 1] < rp[v] || rp[v + 1] > rp[n]) return CC_ERR_INVALID_GRAPH;
+  if (rp[n] && !col) return CC_ERR_ARG;
   unsigned int md = 0;
   for (uint32_t v = 0; v < n; ++v) {
-    if (rp[v + 1] < rp[v]) return CC_ERR_INVALID_GRAPH;
     for (uint32_t e = rp[v]; e < rp[v + 1]; ++e) {
       if (col[e] >= n || col[e] == v) return CC_ERR_INVALID_GRAPH;
       if (e > rp[v] && col[e] <= col[e - 1]) return CC_ERR_INVALID_GRAPH;
@@ -107,7 +119,6 @@ extern "C" cc_status cc_enumerate_noalloc(uint32_t n, const uint32_t* row_ptr, c
                                           uint64_t* out_tcount) {
   if (!row_ptr || !out_hist || !out_hash) return CC_ERR_ARG;
   if (n > kMaxN) return CC_ERR_UNSUPPORTED;
-  if (row_ptr[n] && !col_idx) return CC_ERR_ARG;
   const unsigned int L = (max_len == 0 || max_len > n) ? n : max_len;
   std::memset(out_hist, 0, sizeof(uint64_t) * (L + 1));
   if (out_tcount) std::memset(out_tcount, 0, sizeof(uint64_t) * (L + 1));

@@ -10,6 +10,8 @@
 // Seeding replaces the |V| * Delta^2 flat thread grid of Algorithm 2 (most of whose
 // threads fall outside the neighbour range) by one thread per (u, x) pair of a
 // relabelled adjacency row; the pairs y > x come out of one mask operation.
+#include <mutex>
+
 #include "cc_internal.cuh"
 
 namespace cc {
@@ -217,8 +219,17 @@ cudaError_t launch_label_single(const unsigned int* row_ptr, const unsigned int*
   const size_t csr_words = (size_t)n + 1 + nnz;
   const int stage = (smem + 4 * csr_words) <= 96 * 1024 ? 1 : 0;
   if (stage) smem += 4 * csr_words;
-  cudaError_t e = cudaFuncSetAttribute(label_single_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
+  // the limit is only raised (a replayed CUDA graph of a larger graph keeps its node's size)
+  static std::mutex mu;
+  static size_t allowed = 0;
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    if (smem > allowed) {
+      cudaError_t e = cudaFuncSetAttribute(label_single_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+      allowed = smem;
+    }
+  }
   label_single_kernel<<<1, 1024, smem, st>>>(row_ptr, col, n, W, perm, perm + n, adj, rtab, nrow, ncol, nsig, stage);
   return cudaGetLastError();
 }
@@ -267,6 +278,16 @@ __global__ void __launch_bounds__(256) seed_bitset_kernel(EngineParams p, unsign
 #pragma unroll
   for (int k = 0; k < W; ++k) {
     ys[k] = au[k] & ~lowx[k];           // y in Adj(u), y > x  (so l(u) < l(x) < l(y))
+    if (p.nparts > 1 && ys[k]) {         // triplet sharding: keep this part's triplets only
+      const unsigned int ox = p.perm[x], ou = p.perm[u];
+      unsigned long long b = ys[k], keep = 0ull;
+      while (b) {
+        const unsigned int y = 64u * k + __ffsll((long long)b) - 1;
+        if (triplet_part(ox, ou, p.perm[y], n, p.nparts) == p.part) keep |= b & (0ull - b);
+        b &= b - 1;
+      }
+      ys[k] = keep;
+    }
     const unsigned long long tri = ys[k] & ax[k];    // (x, y) in E: triangle
     paths[k] = (L > 3) ? (ys[k] & ~ax[k]) : 0ull;    // otherwise an initial chordless path
     ntri += __popcll(tri);
@@ -368,9 +389,12 @@ __global__ void __launch_bounds__(256) seed_csr_kernel(EngineParams p, unsigned 
   }
   unsigned long long ntri = 0, hacc = 0;
   unsigned int npath = 0;
+  const bool split = p.nparts > 1;
+  const unsigned int ox = split && active ? p.perm[x] : 0u, ou = split && active ? p.perm[u] : 0u;
   if (active && L >= 3) {
     for (unsigned int f = e + 1; f < rend; ++f) {  // rows are sorted: y > x
       const unsigned int y = p.ncol[f];
+      if (split && triplet_part(ox, ou, p.perm[y], n, p.nparts) != p.part) continue;
       if (csr_adjacent(p.nrow, p.ncol, x, y)) {
         ++ntri;
         hacc += mix64(p.rtab[x] + p.rtab[u] + p.rtab[y] + 3ull * kGamma);
@@ -399,6 +423,7 @@ __global__ void __launch_bounds__(256) seed_csr_kernel(EngineParams p, unsigned 
     unsigned long long slot = base;
     for (unsigned int f = e + 1; f < rend; ++f) {
       const unsigned int y = p.ncol[f];
+      if (split && triplet_part(ox, ou, p.perm[y], n, p.nparts) != p.part) continue;
       if (csr_adjacent(p.nrow, p.ncol, x, y)) continue;
       if (slot >= stride) { set_err(p.ctl, kDevSeedCap, 0); break; }
       R0[slot] = make_uint4(x | (u << 16), y | 0xFFFF0000u, 0xFFFFFFFFu, 0xFFFFFFFFu);

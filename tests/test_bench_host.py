@@ -1,5 +1,5 @@
-"""Host-side logic of bench.py (no GPU): the reading of a per-step trace into the levels
-that two-level steps expanded without storing, and the algorithmic bytes that follow."""
+"""Host-side logic of bench.py (no GPU): algorithmic bytes per stored path, the roofline
+arithmetic, the exchange of per-rank results, and the reference arm's JSON line."""
 import importlib.util
 import os
 from types import SimpleNamespace
@@ -16,27 +16,32 @@ def _bench():
     return mod
 
 
-def test_unstored_levels_from_trace():
+def test_algorithmic_bytes_counts_every_stored_path():
     b = _bench()
     tc = np.array([0, 0, 0, 5, 7, 9, 4, 0], dtype=np.uint64)
-    assert b.unstored_levels(tc, [5, 7, 9, 4]) == set()      # one level per step
-    assert b.unstored_levels(tc, [5, 16, 4]) == {5}          # t=4 step also expanded t=5
-    assert b.unstored_levels(tc, [12, 13]) == {4, 6}
-    assert b.unstored_levels(tc, [3, 2, 7, 9, 4]) == set()   # chunked steps: not resolved
-    assert b.unstored_levels(tc, [5, 7]) == set()            # incomplete trace
+    # bitset records: 16 bytes for one word (n <= 64), 32 for two, 48 for four; each stored
+    # path written once and read once
+    assert b.algorithmic_bytes(tc, 60, 1) == 2 * 16 * 25
+    assert b.algorithmic_bytes(tc, 100, 1) == 2 * 32 * 25
+    assert b.algorithmic_bytes(tc, 200, 1) == 2 * 48 * 25
+    # CSR records: u16 ids padded to 8 (16 bytes up to 8 vertices, 32 up to 16)
+    tc2 = np.zeros(12, dtype=np.uint64)
+    tc2[3], tc2[8], tc2[9], tc2[11] = 5, 2, 3, 1
+    assert b.algorithmic_bytes(tc2, 2000, 2) == 2 * (16 * 5 + 16 * 2 + 32 * 3 + 32 * 1)
 
 
-def test_algorithmic_bytes_counts_stored_levels():
+def test_roofline_of_a_known_kernel():
     b = _bench()
-    tc = np.array([0, 0, 0, 5, 7, 9, 4, 0], dtype=np.uint64)
-    bitset = SimpleNamespace(tcount=tc, info=SimpleNamespace(mode=1))
-    # 20-byte records: every stored path read once, every one after the triplets written once
-    assert b.algorithmic_bytes(bitset, 60) == 20 * (2 * 25 - 5)
-    assert b.algorithmic_bytes(bitset, 60, {5}) == 20 * (2 * 16 - 5)
-    assert b.algorithmic_bytes(bitset, 100) == 28 * (2 * 25 - 5)
-    csr = SimpleNamespace(tcount=tc, info=SimpleNamespace(mode=2))
-    # u16 ids padded to 8: 16 bytes for t <= 8
-    assert b.algorithmic_bytes(csr, 2000) == 16 * 2 * 25 - 16 * 5
+    r = b.roofline("k", 2.0e9, 1.0, 1e6, "no_such_profile")
+    peak, _ = b._peaks()
+    assert abs(r["achieved"] - 2000.0) < 1e-9 and abs(r["frac"] - 2000.0 / peak) < 1e-12
+    assert r["traffic"] is None and r["unit"] == "GB/s"
+
+
+def test_sum_results_without_ranks_wraps_the_hash():
+    b = _bench()
+    h, hh = b.sum_results(np.array([0, 0, 0, 4], dtype=np.uint64), (1 << 64) + 5, None)
+    assert h.tolist() == [0, 0, 0, 4] and hh == 5
 
 
 def _run_bench(args, env_extra=None):
@@ -55,13 +60,24 @@ def _run_bench(args, env_extra=None):
 def test_reference_arm_json_line():
     # the reference arm times the CPU oracle: one JSON line with the contract's keys
     (line,) = _run_bench(["--impl", "reference", "--workload", "grid6", "--steps", "2", "--warmup", "1"])
+    _check_reference_line(line)
+    assert line["config"]["workload"].startswith("grid 6x6")
+
+
+def test_reference_arm_batch_workload():
+    # the default workload: a rotating sample of the batch's graphs per step
+    (line,) = _run_bench(["--impl", "reference", "--steps", "1", "--warmup", "1", "--batch-count", "1024"])
+    _check_reference_line(line)
+    assert line["config"]["workload"].startswith("1024 graphs of the seeded batch mixture")
+
+
+def _check_reference_line(line):
     assert line["impl"] == "reference" and line["metric"] == "chordless cycles/s" and line["unit"] == "cycles/s"
-    assert line["value"] > 0 and line["higher_is_better"] is True and line["steps"] == 2 and line["warmup"] == 1
+    assert line["value"] > 0 and line["higher_is_better"] is True and line["steps"] >= 1 and line["warmup"] == 1
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
     assert line["cpu_baseline"]["value"] == line["value"] and line["cpu_baseline"]["sample"]
     assert line["e2e"] == {"value": line["value"], "unit": "cycles/s", "h2d_bytes_per_step": 0,
                            "d2h_bytes_per_step": 0}
-    assert line["config"]["workload"].startswith("grid 6x6")
 
 
 def test_reference_arm_other_ranks_exit_quietly():

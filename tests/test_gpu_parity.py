@@ -309,10 +309,44 @@ def test_batch_full_mixture_sampled(ctx):
     pick = [i for i, g in enumerate(graphs) if g.meta["family"] == "grid"]
     rng = np.random.default_rng(2024)
     gnp_idx = [i for i, g in enumerate(graphs) if g.meta["family"] == "gnp"]
-    pick += sorted(rng.choice(gnp_idx, 24, replace=False).tolist())
+    pick += sorted(rng.choice(gnp_idx, 256, replace=False).tolist())
     sub = [graphs[i] for i in pick]
     _check_batch(sub, _oracle_many(sub), hist[pick], hsh[pick], paths[pick])
-    assert (done >= 0).all()
+    # per-graph completion: inside the batch's device time; 0 exactly for graphs with no
+    # stored path (finished by seeding), positive for the others
+    seeded = np.array([int(paths[i]) > 0 for i in range(len(graphs))])
+    assert (done[~seeded] == 0).all()
+    assert (done[seeded] > 0).all()
+    assert done.max() <= info.ms_proc * 1000.0 + 1.0
+
+
+def test_batch_resident_set_runs(cc, ctx):
+    # cc_batch_load once, cc_batch_run twice with different length bounds: each run equals
+    # cc_batch_submit of the same graphs and the oracle
+    graphs = I.mixture(300, 41)
+    with ctx.load_batch(graphs) as bs:
+        for L in (8, 6, 8):
+            hist, hsh, paths, done, info = bs.run(max_len=L)
+            h2, s2, p2, _, _ = ctx.batch(graphs, max_len=L)
+            assert (hist == h2).all() and (hsh == s2).all() and (paths == p2).all()
+            _check_batch(graphs, _oracle_many(graphs, L), hist, hsh, paths)
+            assert info.ms_total >= info.ms_proc >= info.ms_engine > 0
+
+
+def test_batch_set_errors(cc, ctx):
+    graphs = I.mixture(8, 3)
+    bad = list(graphs)
+    bad[5] = I.grid(9, 9)  # 81 vertices: beyond the batch limit
+    s, h, idx = cc.cc_batch_load(ctx.handle, I.pack(bad))
+    assert s == cc.CC_ERR_UNSUPPORTED and idx == 5 and not h
+    with ctx.load_batch(graphs) as bs:
+        s, bid = cc.cc_batch_run(bs.handle, 0)
+        assert s == cc.CC_OK
+        s2, _ = cc.cc_batch_run(bs.handle, 0)  # one batch in flight per context
+        assert s2 == cc.CC_ERR_ARG
+    # freeing the set waited for its batch; the context is usable again
+    hist, hsh, paths, done, info = ctx.batch(graphs)
+    _check_batch(graphs, _oracle_many(graphs), hist, hsh, paths)
 
 
 def test_batch_alone_equals_mixed(ctx):
@@ -414,3 +448,48 @@ def test_two_level_steps_equal_single_levels(cc):
         for g in graphs[7:]:
             _same(a.enumerate(g), oracle.enumerate_cycles(g))
         _same(a.enumerate(graphs[4], max_len=9), oracle.enumerate_cycles(graphs[4], max_len=9))
+
+
+# ------------------------------------------------------------------ triplet sharding
+
+@pytest.mark.parametrize("g,L", [(I.grid(8, 8), 0), (I.gnp(60, 0.15, 7), 0), (I.gnp(100, 0.08, 3), 0),
+                                 (I.gnp(200, 0.03, 4), 0), (I.gnm(2000, 4000, 11), 9), (I.grid(5, 6), 0)])
+def test_enumerate_part_equals_oracle_part(ctx, g, L):
+    # each part equals the oracle's part of the same triplet split, and the parts add up
+    nparts = 3
+    whole = oracle.enumerate_cycles(g, max_len=L)
+    with ctx.load(g) as lg:
+        hist = np.zeros_like(whole.hist)
+        tc = np.zeros_like(whole.tcount)
+        hsh = 0
+        for part in range(nparts):
+            r = lg.enumerate(L, part=part, nparts=nparts)
+            ref = oracle.enumerate_cycles(g, max_len=L, part=part, nparts=nparts)
+            _same(r, ref)
+            hist += r.hist
+            tc += r.tcount
+            hsh = (hsh + r.hash) % 2 ** 64
+        assert hist.tolist() == whole.hist.tolist() and hsh == whole.hash and tc.tolist() == whole.tcount.tolist()
+
+
+def test_enumerate_part_csr_mode_and_cycles(cc):
+    g = I.gnp(40, 0.12, 9)
+    with cc.Context(frontier_bytes=1 << 30, mode=cc.CC_MODE_CSR) as c, c.load(g) as lg:
+        allc = []
+        for part in range(2):
+            r = lg.enumerate(0, cycles=True, part=part, nparts=2)
+            ref = oracle.enumerate_cycles(g, cycles=True, part=part, nparts=2)
+            _same(r, ref)
+            assert sorted(r.cycles) == sorted(ref.cycles)
+            allc += r.cycles
+        assert sorted(allc) == sorted(oracle.enumerate_cycles(g, cycles=True).cycles)
+
+
+def test_enumerate_part_arguments(cc, ctx):
+    with ctx.load(I.grid(4, 4)) as lg:
+        s, *_ = cc.cc_enumerate(lg.handle, 16, 0, True, None, 2, 2)
+        assert s == cc.CC_ERR_ARG
+        s, *_ = cc.cc_enumerate(lg.handle, 16, 0, True, None, 1, 0)
+        assert s == cc.CC_ERR_ARG
+        r = lg.enumerate(0, part=0, nparts=1)
+        assert r.total == oracle.enumerate_cycles(I.grid(4, 4)).total

@@ -371,9 +371,22 @@ def test_relabelling_invariance(seed):
 
 @pytest.mark.parametrize("nparts", [2, 3, 7])
 def test_parts_add_up(nparts):
-    g = I.gnp(30, 0.2, 5)
-    whole = oracle.enumerate_cycles(g)
-    parts = [oracle.enumerate_cycles(g, part=p, nparts=nparts) for p in range(nparts)]
-    assert sum(p.hist for p in parts).tolist() == whole.hist.tolist()
-    assert sum(p.tcount for p in parts).tolist() == whole.tcount.tolist()
-    assert sum(p.hash for p in parts) % 2 ** 64 == whole.hash
+    for g, L in [(I.gnp(30, 0.2, 5), 0), (I.gnp(24, 0.35, 6), 0), (I.grid(4, 5), 0), (I.gnp(40, 0.15, 8), 9)]:
+        whole = oracle.enumerate_cycles(g, max_len=L)
+        parts = [oracle.enumerate_cycles(g, max_len=L, part=p, nparts=nparts) for p in range(nparts)]
+        assert sum(p.hist for p in parts).tolist() == whole.hist.tolist()
+        assert sum(p.tcount for p in parts).tolist() == whole.tcount.tolist()
+        assert sum(p.hash for p in parts) % 2 ** 64 == whole.hash
+        # a real split: no part holds everything (these graphs have many triplets)
+        assert all(p.total < whole.total for p in parts)
+
+
+@pytest.mark.parametrize("chunk", range(2))
+def test_parts_partition_the_definition(chunk):
+    # the parts' cycle lists are disjoint and together equal the brute-force cycle set
+    for g in _small_graphs(30, 7000 + 100 * chunk):
+        ref = sorted(oracle.bruteforce(g, cycles=True).cycles)
+        got = []
+        for p in range(3):
+            got += oracle.enumerate_cycles(g, cycles=True, part=p, nparts=3).cycles
+        assert sorted(got) == ref

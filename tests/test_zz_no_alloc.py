@@ -11,6 +11,7 @@ import ctypes
 import numpy as np
 import pytest
 
+import oracle
 from paper_1410_4876_gb300 import inputs as I
 
 pytestmark = pytest.mark.gpu
@@ -64,4 +65,38 @@ def test_noalloc_rejects_unsorted_rows(cc):
     rp, cl = g.row_ptr.copy(), g.col.copy()
     cl[rp[4]:rp[5]] = cl[rp[4]:rp[5]][::-1]
     s, *_ = _noalloc(cc, I.Graph(g.n, rp, cl))
+    assert s == cc.CC_ERR_INVALID_GRAPH
+
+
+def test_noalloc_chunks_a_frontier_larger_than_the_array(cc):
+    # the 8 x 8 grid's two largest levels hold about 5.7 M paths (over 100 MB of records),
+    # more than the array's frontier: the expansion must go depth-first in chunks.  A
+    # context with a frontier of the array's size shows that such a run spills.
+    g = I.grid(8, 8)
+    with cc.Context(frontier_bytes=63 << 20) as ctx:
+        assert ctx.enumerate(g).info.spilled == 1
+    ref = oracle.enumerate_cycles(g)
+    for _ in range(2):
+        s, hist, h, tc = _noalloc(cc, g)
+        assert s == cc.CC_OK, cc.status_str(s)
+        assert hist.tolist() == ref.hist.tolist() and h == ref.hash and tc.tolist() == ref.tcount.tolist()
+
+
+def test_noalloc_capacity_error_then_recovers(cc):
+    # K_{128,128}: its initial triplets (up to 127 * 16384 / 2) need more than half of the
+    # array; the call fails cleanly and the next call is exact
+    s, *_ = _noalloc(cc, I.complete_bipartite(128, 128))
+    assert s == cc.CC_ERR_CAPACITY
+    g = I.gnp(60, 0.15, 7)
+    ref = oracle.enumerate_cycles(g)
+    s, hist, h, tc = _noalloc(cc, g)
+    assert s == cc.CC_OK and hist.tolist() == ref.hist.tolist() and h == ref.hash
+
+
+def test_noalloc_rejects_bogus_offsets(cc):
+    # row_ptr[n] beyond n (n - 1) is refused before col_idx is read
+    g = I.grid(3, 3)
+    rp = g.row_ptr.copy()
+    rp[-1] = 9 * 8 + 1
+    s, *_ = _noalloc(cc, I.Graph(g.n, rp, g.col))
     assert s == cc.CC_ERR_INVALID_GRAPH
