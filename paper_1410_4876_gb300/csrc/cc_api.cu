@@ -742,8 +742,13 @@ static cc_status batch_run(cc_batch_set* bs, uint32_t max_len, cc_batch_id* out)
   cc_status s;
   if ((s = ensure_arena(c))) return s;
   if ((s = ensure_frames(c, 70))) return s;
-  // work pack: adj | rtab | Lg | hist | hash | tcount | last | ts
-  b.ts_cap = 1u << 16;
+  // per-step trace (end time and paths expanded of each step) in the context's trace buffer
+  if (!c->d_trace) {
+    if ((s = dev_alloc(c, (void**)&c->d_trace, 16ull * kTraceCap))) return s;
+    c->trace_cap = kTraceCap;
+  }
+  b.ts_cap = c->trace_cap;
+  // work pack: adj | rtab | Lg | hist | hash | tcount | last
   auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
   size_t off = 0;
   const size_t o_adj = off; off = al(off + 8ull * 64 * count);
@@ -753,7 +758,6 @@ static cc_status batch_run(cc_batch_set* bs, uint32_t max_len, cc_batch_id* out)
   const size_t o_hash = off; off = al(off + 8ull * count);
   const size_t o_tc = off; off = al(off + 8ull * kMultiHistStride * count);
   const size_t o_last = off; off = al(off + 4ull * count);
-  const size_t o_ts = off; off = al(off + 8ull * b.ts_cap);
   const size_t total = off;
   if (b.d_pack_bytes < total) {
     dev_free(c, b.d_pack);
@@ -785,7 +789,8 @@ static cc_status batch_run(cc_batch_set* bs, uint32_t max_len, cc_batch_id* out)
   p.hash = reinterpret_cast<unsigned long long*>(base + o_hash);
   p.tcount = reinterpret_cast<unsigned long long*>(base + o_tc);
   p.last_step = reinterpret_cast<unsigned int*>(base + o_last);
-  p.step_ts = reinterpret_cast<unsigned long long*>(base + o_ts);
+  p.step_ts = c->d_trace;
+  p.step_rec = c->d_trace + c->trace_cap;
   p.step_ts_cap = b.ts_cap;
   p.spin_limit = c->opts.spin_limit ? c->opts.spin_limit : kDefaultSpin;
   p.fresh = 1;
@@ -800,7 +805,7 @@ static cc_status batch_run(cc_batch_set* bs, uint32_t max_len, cc_batch_id* out)
   const int grid = engine_grid(c, Kind::Multi, block, 0);
   if (grid <= 0) return CC_ERR_CUDA;
   ok(cudaEventRecord(c->ev0, st));
-  ok(cudaMemsetAsync(base + o_hist, 0, o_ts - o_hist, st));
+  ok(cudaMemsetAsync(base + o_hist, 0, total - o_hist, st));
   ok(cudaMemsetAsync(c->ctl, 0, sizeof(Control), st));
   ok(launch_label_seed_multi(reinterpret_cast<unsigned int*>(in + bs->o_rows),
                              reinterpret_cast<unsigned long long*>(in + bs->o_roff),
@@ -951,5 +956,6 @@ extern "C" cc_status cc_batch_poll(cc_context* c, cc_batch_id id, uint32_t timeo
   }
   if (info) *info = ri;
   c->last = ri;
+  c->last_t_start = h.t_start;  // cc_get_trace after a batch: steps timed from its start
   return s;
 }

@@ -1057,17 +1057,27 @@ __device__ __forceinline__ void process_bitset_fused(const EngineParams& p, cons
 // statistics (paths expanded, children and closings per (slot, length)) are accumulated
 // in lane order as runs of one key, as in the per-lane form; a closing's hash is added to
 // its slot's sum by one atomic per distinct slot among the lanes of a round.
+//
+// Work distribution: a warp takes contiguous chunks of the step's records from a step
+// counter (one atomic per chunk), so its rounds mostly stay inside one graph's run of
+// records while the chunks balance the load between warps.  The rows, r-table and L' of
+// the graph a warp is working on are staged in the warp's shared memory when the graph
+// changes; records of any other graph in the same round read them from global memory.
 template <int NT>
 __device__ __forceinline__ void process_multi_flat(const EngineParams& p, const StepPlan& pl,
                                                    const unsigned long long* adj, const unsigned long long* rtab) {
   constexpr int P = KindTraits<Kind::Multi>::P;
   constexpr unsigned int CL = FlatSmem<1, P, NT>::CL;
   __shared__ FlatSmem<1, P, NT> fs;
+  __shared__ unsigned long long s_gadj[NT / 32][64];
+  __shared__ unsigned long long s_grt[NT / 32][64];
   const unsigned int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   unsigned long long* snb = fs.nb[wid];
   unsigned long long* sh = fs.h[wid];
   unsigned int* smeta = fs.v1[wid];  // v1 | t << 6 | g << 12 | (t + 2 < L'_g) << 31
   unsigned int* sl = fs.list[wid];
+  unsigned long long* ga = s_gadj[wid];
+  unsigned long long* gr = s_grt[wid];
   const unsigned long long ss = pl.src_stride, ds = pl.dst_stride;
   const unsigned long long* sB = reinterpret_cast<const unsigned long long*>(p.arena + pl.src_base);
   const unsigned long long* sH = sB + ss;
@@ -1080,7 +1090,14 @@ __device__ __forceinline__ void process_multi_flat(const EngineParams& p, const 
   unsigned long long nx = 0;
   StatRun run;
   run.key = 0xFFFFFFFFu;
-  const unsigned long long T = (unsigned long long)gridDim.x * blockDim.x;
+  unsigned int cg = 0xFFFFFFFFu;  // graph staged in ga / gr
+  unsigned int cL = 0;            // its L'
+  auto A = [&](unsigned int g, unsigned int v) -> unsigned long long {
+    return g == cg ? ga[v] : __ldg(adj + (unsigned long long)g * 64ull + v);
+  };
+  auto R = [&](unsigned int g, unsigned int v) -> unsigned long long {
+    return g == cg ? gr[v] : __ldg(rtab + (unsigned long long)g * 64ull + v);
+  };
 
   // children entries [0, n) take slots base + [0, n)
   auto flush_children = [&](unsigned int n, unsigned long long base) {
@@ -1089,13 +1106,13 @@ __device__ __forceinline__ void process_multi_flat(const EngineParams& p, const 
     for (unsigned int i = lane; i < n; i += 32) {
       const unsigned int e = sl[i], pj = e >> 8, v = e & 0xFFu;
       const unsigned int meta = smeta[pj], v1 = meta & 63u, tt = (meta >> 6) & 63u, g = (meta >> 12) & 0x7FFFFu;
-      const unsigned long long go = (unsigned long long)g * 64ull, slot = base + i;
+      const unsigned long long slot = base + i;
       if (slot < ds) {
         const unsigned long long nb = snb[pj];
         dB[slot] = nb;
-        dH[slot] = sh[pj] + __ldg(rtab + go + v);
+        dH[slot] = sh[pj] + R(g, v);
         dM[slot] = v1 | (v << 6) | ((tt + 1) << 12) | (g << 18);
-        if (meta >> 31) nx += __popcll(__ldg(adj + go + v) & ~nb & ~__ldg(adj + go + v1));
+        if (meta >> 31) nx += __popcll(A(g, v) & ~nb & ~A(g, v1));
       } else {
         set_err(p.ctl, kDevBounds, 1);
       }
@@ -1112,10 +1129,10 @@ __device__ __forceinline__ void process_multi_flat(const EngineParams& p, const 
         const unsigned int e = sl[i], pj = e >> 8, v = e & 0xFFu;
         const unsigned int meta = smeta[pj], tt = (meta >> 6) & 63u;
         g = (meta >> 12) & 0x7FFFFu;
-        h = mix64(sh[pj] + __ldg(rtab + (unsigned long long)g * 64ull + v) + (unsigned long long)(tt + 1) * kGamma);
+        h = mix64(sh[pj] + R(g, v) + (unsigned long long)(tt + 1) * kGamma);
       }
-      // a frontier keeps each graph's records together: usually every active lane of a
-      // round closes cycles of one slot (one warp sum, one atomic); otherwise per lane
+      // usually every active lane of a round closes cycles of one slot (one warp sum,
+      // one atomic); otherwise per lane
       const unsigned int g0 = __shfl_sync(0xffffffffu, g, 0);  // lane 0 is active (n > r0)
       if (__all_sync(0xffffffffu, g == g0 || i >= n)) {
         const unsigned long long sum = warp_sum_u64(h);
@@ -1161,68 +1178,89 @@ __device__ __forceinline__ void process_multi_flat(const EngineParams& p, const 
     }
   };
 
-  // a warp takes pf * 32 consecutive records per round (a frontier keeps each graph's
-  // records together, so the per-slot statistics of a round are mostly one run)
   const unsigned int pf = p.pf >= 1 && p.pf <= (unsigned)P ? p.pf : (unsigned)P;
-  const unsigned long long gwarp = ((unsigned long long)wid * gridDim.x + blockIdx.x) * 32ull * pf;
-  for (unsigned long long wb = pl.begin + gwarp; wb < pl.end; wb += pf * T) {
-    const unsigned long long t0 = wb + lane;
-    unsigned long long ch[P];
-    unsigned int key[P], nc[P], nk[P];
+  const unsigned int RW = pf * 32;  // records per warp round
+  const unsigned long long total = pl.end - pl.begin;
+  const unsigned long long nwarps = (unsigned long long)gridDim.x * (NT / 32);
+  // chunks of about an eighth of a warp's share, between 1 and 16 rounds
+  unsigned long long chunk = (total / (nwarps * 8) + RW - 1) / RW * RW;
+  chunk = chunk < RW ? RW : (chunk > 16ull * RW ? 16ull * RW : chunk);
+  for (;;) {
+    unsigned long long c0 = 0;
+    if (lane == 0) c0 = atomicAdd(&p.ctl->take[s % 3], chunk);
+    c0 = __shfl_sync(0xffffffffu, c0, 0);
+    if (c0 >= total) break;
+    const unsigned long long cend = pl.begin + min(c0 + chunk, total);
+    for (unsigned long long wb = pl.begin + c0; wb < cend; wb += RW) {
+      // the graph of the round's first record (always valid): stage it if it changed
+      const unsigned int g0 = ldcg32(sM + wb) >> 18;
+      if (g0 != cg) {
+        __syncwarp();
+        ga[lane] = __ldg(adj + (unsigned long long)g0 * 64ull + lane);
+        ga[lane + 32] = __ldg(adj + (unsigned long long)g0 * 64ull + lane + 32);
+        gr[lane] = __ldg(rtab + (unsigned long long)g0 * 64ull + lane);
+        gr[lane + 32] = __ldg(rtab + (unsigned long long)g0 * 64ull + lane + 32);
+        cL = p.Lg[g0];
+        cg = g0;
+        __syncwarp();
+      }
+      const unsigned long long t0 = wb + lane;
+      unsigned long long ch[P];
+      unsigned int key[P], nc[P], nk[P];
 #pragma unroll
-    for (int j = 0; j < P; ++j) {
-      const unsigned long long i = t0 + (unsigned long long)j * 32ull;
-      const bool valid = (unsigned)j < pf && i < pl.end;
-      const unsigned long long B = valid ? ldcg64(sB + i) : ~0ull;
-      const unsigned long long H = valid ? ldcg64(sH + i) : 0ull;
-      const unsigned int M = valid ? ldcg32(sM + i) : 0u;
-      const unsigned int v1 = M & 63u, vt = (M >> 6) & 63u, tt = (M >> 12) & 63u, g = M >> 18;
-      const unsigned long long go = (unsigned long long)g * 64ull;
-      const unsigned int Lr = valid ? p.Lg[g] : 0u;
-      const unsigned long long at = __ldg(adj + go + vt), a1 = __ldg(adj + go + v1);
-      const unsigned long long cand = at & ~B;
-      m[j] = (tt + 1 <= Lr) ? (cand & a1) : 0ull;
-      ch[j] = (store && tt + 1 < Lr) ? (cand & ~a1) : 0ull;
-      const unsigned int pj = j * 32 + lane;
-      snb[pj] = B | at;
-      sh[pj] = H;
-      smeta[pj] = v1 | (tt << 6) | (g << 12) | ((tt + 2 < Lr) ? 0x80000000u : 0u);
-      key[j] = valid ? (g << 6 | tt) : 0xFFFFFFFFu;
-      nc[j] = __popcll(m[j]);
-      nk[j] = __popcll(ch[j]);
-    }
-    // per (slot, length) counts, as runs of one key (no hash here: closings add theirs)
+      for (int j = 0; j < P; ++j) {
+        const unsigned long long i = t0 + (unsigned long long)j * 32ull;
+        const bool valid = (unsigned)j < pf && i < cend;
+        const unsigned long long B = valid ? ldcg64(sB + i) : ~0ull;
+        const unsigned long long H = valid ? ldcg64(sH + i) : 0ull;
+        const unsigned int M = valid ? ldcg32(sM + i) : 0u;
+        const unsigned int v1 = M & 63u, vt = (M >> 6) & 63u, tt = (M >> 12) & 63u, g = M >> 18;
+        const unsigned int Lr = valid ? (g == cg ? cL : p.Lg[g]) : 0u;
+        const unsigned long long at = A(g, vt), a1 = A(g, v1);
+        const unsigned long long cand = at & ~B;
+        m[j] = (tt + 1 <= Lr) ? (cand & a1) : 0ull;
+        ch[j] = (store && tt + 1 < Lr) ? (cand & ~a1) : 0ull;
+        const unsigned int pj = j * 32 + lane;
+        snb[pj] = B | at;
+        sh[pj] = H;
+        smeta[pj] = v1 | (tt << 6) | (g << 12) | ((tt + 2 < Lr) ? 0x80000000u : 0u);
+        key[j] = valid ? (g << 6 | tt) : 0xFFFFFFFFu;
+        nc[j] = __popcll(m[j]);
+        nk[j] = __popcll(ch[j]);
+      }
+      // per (slot, length) counts, as runs of one key (no hash here: closings add theirs)
 #pragma unroll
-    for (int j = 0; j < P; ++j) {
-      const unsigned int k = key[j];
-      const bool v = k != 0xFFFFFFFFu;
-      const bool m0 = v && k == run.key;
-      if (m0) run.add(nc[j], nk[j], 0ull);
-      const unsigned int rest = __ballot_sync(0xffffffffu, v && !m0);
-      if (rest) {
-        run.flush(p, s);
-        run.key = __shfl_sync(0xffffffffu, k, 31 - __clz(rest));
-        const bool m1 = v && !m0 && k == run.key;
-        if (m1) run.add(nc[j], nk[j], 0ull);
-        unsigned int pending = __ballot_sync(0xffffffffu, v && !m0 && !m1);
-        while (pending) {
-          const int leader = __ffs(pending) - 1;
-          const unsigned int lk = __shfl_sync(0xffffffffu, k, leader);
-          const bool mine = k == lk;
-          const unsigned int grp = __ballot_sync(0xffffffffu, mine);
-          StatRun one;
-          one.key = lk;
-          if (mine) one.add(nc[j], nk[j], 0ull);
-          one.flush(p, s);
-          pending &= ~grp;
+      for (int j = 0; j < P; ++j) {
+        const unsigned int k = key[j];
+        const bool v = k != 0xFFFFFFFFu;
+        const bool m0 = v && k == run.key;
+        if (m0) run.add(nc[j], nk[j], 0ull);
+        const unsigned int rest = __ballot_sync(0xffffffffu, v && !m0);
+        if (rest) {
+          run.flush(p, s);
+          run.key = __shfl_sync(0xffffffffu, k, 31 - __clz(rest));
+          const bool m1 = v && !m0 && k == run.key;
+          if (m1) run.add(nc[j], nk[j], 0ull);
+          unsigned int pending = __ballot_sync(0xffffffffu, v && !m0 && !m1);
+          while (pending) {
+            const int leader = __ffs(pending) - 1;
+            const unsigned int lk = __shfl_sync(0xffffffffu, k, leader);
+            const bool mine = k == lk;
+            const unsigned int grp = __ballot_sync(0xffffffffu, mine);
+            StatRun one;
+            one.key = lk;
+            if (mine) one.add(nc[j], nk[j], 0ull);
+            one.flush(p, s);
+            pending &= ~grp;
+          }
         }
       }
-    }
-    list_and_work(false);
-    if (store) {
+      list_and_work(false);
+      if (store) {
 #pragma unroll
-      for (int j = 0; j < P; ++j) m[j] = ch[j];
-      list_and_work(true);
+        for (int j = 0; j < P; ++j) m[j] = ch[j];
+        list_and_work(true);
+      }
     }
   }
   run.flush(p, s);
@@ -2093,6 +2131,7 @@ __global__ void __launch_bounds__(NT, NT >= 1024 ? 1 : KindTraits<K>::minB) engi
     if (blockIdx.x == 0 && tid == 0) {
       cntp[(s + 1) % 3] = 0;
       nxtp[(s + 1) % 3] = 0;
+      p.ctl->take[(s + 1) % 3] = 0;
       if (p.cyc_stream) p.ctl->ncl[(s + 1) % 3] = 0;
     }
     if (p.cluster) {

@@ -85,6 +85,7 @@ struct Control {
   alignas(128) unsigned long long cnt[3];  // children written in step s (index s % 3)
   unsigned long long nxt[3];               // children-of-children of step s (next frame size)
   unsigned long long ncl[3];               // streamed CSR lists: closing bound of step s's children
+  alignas(128) unsigned long long take[3]; // batch: records of step s handed out to warps so far
   alignas(128) unsigned int bar_gen;       // barrier generation (released by the last group)
   int err;                                 // first device error (kDev*), 0 if none
   int err_info;
