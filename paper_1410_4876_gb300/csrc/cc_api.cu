@@ -797,7 +797,7 @@ static cc_status batch_run(cc_batch_set* bs, uint32_t max_len, cc_batch_id* out)
   p.pf = c->opts.paths_per_thread;
   p.fuse_ok = (c->opts.flags & CC_FLAG_NO_FUSE) ? 0u : 1u;
   const unsigned long long seed_stride = round_up(bs->tb_total + 8, 8);
-  const unsigned long long seed_bytes = bitset_region_bytes(seed_stride, 1);
+  const unsigned long long seed_bytes = multi_region_bytes(seed_stride);
   if (seed_bytes > c->arena_bytes / 2) return CC_ERR_CAPACITY;
   p.seed_stride = seed_stride;
   p.seed_bytes = seed_bytes;
@@ -948,10 +948,9 @@ extern "C" cc_status cc_batch_poll(cc_context* c, cc_batch_id id, uint32_t timeo
     ri.cycles += cg;
     if (done_us) {
       // a graph is finished at the end of the last step that expanded one of its paths
-      // (graphs with no stored path finish with seeding: 0)
+      // (hl = 1 + that step; graphs with no stored path finish with seeding: 0)
       const unsigned int ls = hl[g];
-      const bool expanded = ht[(size_t)g * kMultiHistStride + 3] != 0;
-      done_us[g] = (expanded && ls < ts.size()) ? ((double)ts[ls] - t_start_ns) / 1000.0 : 0.0;
+      done_us[g] = (ls > 0 && ls - 1 < ts.size()) ? ((double)ts[ls - 1] - t_start_ns) / 1000.0 : 0.0;
     }
   }
   if (info) *info = ri;

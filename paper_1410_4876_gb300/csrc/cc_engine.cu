@@ -82,7 +82,7 @@ struct KindTraits {
   // register allocation must allow (4 blocks = 64 registers per thread, 3 = 85, 2 = 128)
   static constexpr int P = K == Kind::Bitset4 ? 1 : (K == Kind::Bitset1 ? 3 : 2);
   static constexpr int minB =
-      (K == Kind::Csr || K == Kind::Csr32) ? 2 : ((K == Kind::Multi || K == Kind::Csr16 || K == Kind::Bitset1) ? 3 : 4);
+      (K == Kind::Csr || K == Kind::Csr32) ? 2 : ((K == Kind::Csr16 || K == Kind::Bitset1) ? 3 : 4);
   // paths per thread per round of the flattened single-graph form (one slot atomic per
   // warp per round)
   static constexpr int PF = K == Kind::Bitset1 ? 3 : (K == Kind::Bitset2 ? 2 : 1);
@@ -93,11 +93,13 @@ struct KindTraits {
 template <Kind K>
 __device__ __forceinline__ unsigned long long region_bytes(unsigned long long stride, unsigned int t_child) {
   if constexpr (KindTraits<K>::csr) return csr_region_bytes(stride, t_child);
+  else if constexpr (KindTraits<K>::multi) return multi_region_bytes(stride);
   else return bitset_region_bytes(stride, KindTraits<K>::W);
 }
 template <Kind K>
 __device__ __forceinline__ unsigned long long record_bytes(unsigned int t_child) {
   if constexpr (KindTraits<K>::csr) return 2ull * csr_rec_u16(t_child);
+  else if constexpr (KindTraits<K>::multi) return 28ull;
   else return 8ull * KindTraits<K>::W + 12ull;
 }
 
@@ -291,39 +293,77 @@ __device__ void commit_step(const EngineParams& p, LocalState& st, unsigned long
 
 // ------------------------------------------------------------------ bitset expansion
 
-// Batch-mode statistics of one (slot, length) key, accumulated per lane; flush() is
-// warp-collective and adds the warp's sums to the slot's histogram, hash, stored-path
-// count and in-flight count with one lane's atomics.
+// Batch-mode statistics of one (slot, length tt) key, accumulated per lane; flush() is
+// warp-collective and adds the warp's sums with one lane's atomics:
+//   hist[tt + 1]   += c        cycles closed by paths of tt vertices
+//   tcount[tt + 1] += k        paths of tt + 1 vertices (children of paths of tt vertices)
+//   hash           += h
+//   live           += st - n   paths stored minus paths expanded (still in flight)
+//   last_step       = s + 1    when a path was expanded
 struct StatRun {
   unsigned int key;
-  unsigned int c = 0, k = 0, n = 0;
+  unsigned int n = 0, k = 0, c = 0, st = 0;
   unsigned long long h = 0;
-  __device__ __forceinline__ void add(unsigned int cc, unsigned int kk, unsigned long long hh) {
-    c += cc;
+  __device__ __forceinline__ void add(unsigned int nn, unsigned int kk, unsigned int cc, unsigned int ss,
+                                      unsigned long long hh) {
+    n += nn;
     k += kk;
-    n += 1;
+    c += cc;
+    st += ss;
     h += hh;
   }
   __device__ __forceinline__ void flush(const EngineParams& p, unsigned long long s) {
-    const unsigned int sc = __reduce_add_sync(0xffffffffu, c);
-    const unsigned int sk = __reduce_add_sync(0xffffffffu, k);
     const unsigned int sn = __reduce_add_sync(0xffffffffu, n);
+    const unsigned int sk = __reduce_add_sync(0xffffffffu, k);
+    const unsigned int sc = __reduce_add_sync(0xffffffffu, c);
+    const unsigned int sst = __reduce_add_sync(0xffffffffu, st);
     const unsigned long long sh = warp_sum_u64(h);
-    if ((threadIdx.x & 31) == 0 && key != 0xFFFFFFFFu && sn) {
+    if ((threadIdx.x & 31) == 0 && key != 0xFFFFFFFFu) {
       const unsigned int g = key >> 6, tt = key & 63u;
       const unsigned long long hb = (unsigned long long)g * kMultiHistStride;
       if (sc) atomicAdd(&p.hist[hb + tt + 1], (unsigned long long)sc);
       if (sh) atomicAdd(&p.hash[g], sh);
       if (sk) atomicAdd(&p.tcount[hb + tt + 1], (unsigned long long)sk);
-      if (p.live)
+      if (p.live && sst != sn)
         atomicAdd(reinterpret_cast<unsigned long long*>(&p.live[g]),
-                  (unsigned long long)((long long)sk - (long long)sn));
-      if (p.last_step) atomicMax(&p.last_step[g], (unsigned int)s);
+                  (unsigned long long)((long long)sst - (long long)sn));
+      if (p.last_step && sn) atomicMax(&p.last_step[g], (unsigned int)s + 1u);
     }
-    c = k = n = 0;
+    n = k = c = st = 0;
     h = 0;
   }
 };
+
+// Adds one value set per lane to the warp's run (lanes with key 0xFFFFFFFF add nothing).
+// Lanes whose key differs from the run's flush it and start a new run with the last such
+// lane's key; a third key in the same call is aggregated over its lanes and flushed at
+// once.  Warp-collective.
+__device__ __forceinline__ void account(StatRun& run, const EngineParams& p, unsigned long long s, unsigned int key,
+                                        unsigned int n, unsigned int k, unsigned int c, unsigned int st,
+                                        unsigned long long h) {
+  const bool v = key != 0xFFFFFFFFu;
+  const bool m0 = v && key == run.key;
+  if (m0) run.add(n, k, c, st, h);
+  const unsigned int rest = __ballot_sync(0xffffffffu, v && !m0);
+  if (rest) {
+    run.flush(p, s);
+    run.key = __shfl_sync(0xffffffffu, key, 31 - __clz(rest));
+    const bool m1 = v && !m0 && key == run.key;
+    if (m1) run.add(n, k, c, st, h);
+    unsigned int pending = __ballot_sync(0xffffffffu, v && !m0 && !m1);
+    while (pending) {
+      const int leader = __ffs(pending) - 1;
+      const unsigned int lk = __shfl_sync(0xffffffffu, key, leader);
+      const bool mine = key == lk;
+      const unsigned int grp = __ballot_sync(0xffffffffu, mine);
+      StatRun one;
+      one.key = lk;
+      if (mine) one.add(n, k, c, st, h);
+      one.flush(p, s);
+      pending &= ~grp;
+    }
+  }
+}
 
 // Algorithm 3 on bitset records.  For a path p = <v1 .. vt> with blocked set B:
 //   cand  = Adj(vt) & ~B      label test (l(v) > l(v2)), v not on p, chord test v2..v_{t-1}
@@ -339,7 +379,7 @@ __device__ __forceinline__ void process_bitset(const EngineParams& p, const Step
                                                unsigned long long* nxtp) {
   constexpr int W = KindTraits<K>::W;
   constexpr int P = KindTraits<K>::P;
-  constexpr bool MULTI = KindTraits<K>::multi;
+  static_assert(!KindTraits<K>::multi, "batch records are expanded by process_multi_flat");
   const unsigned int tid = threadIdx.x;
   const unsigned long long ss = pl.src_stride, ds = pl.dst_stride;
   const unsigned long long* sB = reinterpret_cast<const unsigned long long*>(p.arena + pl.src_base);
@@ -351,10 +391,8 @@ __device__ __forceinline__ void process_bitset(const EngineParams& p, const Step
   const bool store = ds != 0;
   const unsigned int t = pl.t, L = p.L;
   const unsigned long long s = pl.s;
-  const bool close_ok1 = t + 1 <= L, next_ok1 = t + 2 < L;
+  const bool close_ok = t + 1 <= L, next_ok = t + 2 < L;
   unsigned long long nx = 0, ncyc = 0, hacc = 0;
-  StatRun run;  // batch mode: the warp's current run of records with one (slot, length)
-  run.key = 0xFFFFFFFFu;
 
   // thread-interleaved grid stride: path i0 + j*T (j < P) for thread gtid, T threads in
   // the grid, so the last round of a step is spread over every thread (no block tiles)
@@ -371,8 +409,6 @@ __device__ __forceinline__ void process_bitset(const EngineParams& p, const Step
     unsigned long long B[P][W], H[P], ch[P][W];
     unsigned int M[P];
     unsigned int nch = 0;
-    unsigned int mcyc[P], mch[P], mkey[P];
-    unsigned long long mh[P];
 #pragma unroll
     for (int j = 0; j < P; ++j) {
       const unsigned long long i = t0 + (unsigned long long)j * T;
@@ -381,80 +417,21 @@ __device__ __forceinline__ void process_bitset(const EngineParams& p, const Step
       for (int k = 0; k < W; ++k) B[j][k] = valid ? ldcg64(sB + k * ss + i) : ~0ull;
       H[j] = valid ? ldcg64(sH + i) : 0ull;
       M[j] = valid ? ldcg32(sM + i) : 0u;
-      unsigned int v1, vt, tt = t, Lr = L;
-      unsigned long long go = 0;
-      if constexpr (MULTI) {
-        v1 = M[j] & 63u;
-        vt = (M[j] >> 6) & 63u;
-        tt = (M[j] >> 12) & 63u;
-        const unsigned int g = M[j] >> 18;
-        go = (unsigned long long)g * 64ull;
-        Lr = valid ? __ldg(p.Lg + g) : 0u;
-      } else {
-        v1 = M[j] & 0xFFFFu;
-        vt = M[j] >> 16;
-      }
-      const bool close_ok = MULTI ? (tt + 1 <= Lr) : close_ok1;
-      const bool store_ok = MULTI ? (store && tt + 1 < Lr) : store;
-      unsigned int cc = 0, nj = 0;
-      unsigned long long hh = 0;
+      const unsigned int v1 = M[j] & 0xFFFFu, vt = M[j] >> 16;
 #pragma unroll
       for (int k = 0; k < W; ++k) {
-        const unsigned long long at = MULTI ? __ldg(adj + go + vt) : adj[(unsigned long long)vt * W + k];
-        const unsigned long long a1 = MULTI ? __ldg(adj + go + v1) : adj[(unsigned long long)v1 * W + k];
+        const unsigned long long at = adj[(unsigned long long)vt * W + k];
+        const unsigned long long a1 = adj[(unsigned long long)v1 * W + k];
         const unsigned long long cand = at & ~B[j][k];
         unsigned long long close = cand & a1;
-        ch[j][k] = store_ok ? (cand & ~a1) : 0ull;
-        nj += __popcll(ch[j][k]);
+        ch[j][k] = store ? (cand & ~a1) : 0ull;
+        nch += __popcll(ch[j][k]);
         if (close_ok) {
-          cc += __popcll(close);
+          ncyc += __popcll(close);
           while (close) {
             const unsigned int v = 64u * k + __ffsll((long long)close) - 1;
             close &= close - 1;
-            const unsigned long long rv = MULTI ? __ldg(rtab + go + v) : rtab[v];
-            hh += mix64(H[j] + rv + (unsigned long long)(tt + 1) * kGamma);
-          }
-        }
-      }
-      nch += nj;
-      if constexpr (MULTI) {
-        mcyc[j] = cc;
-        mh[j] = hh;
-        mch[j] = nj;
-        mkey[j] = valid ? ((M[j] >> 18) << 6 | tt) : 0xFFFFFFFFu;
-      } else {
-        ncyc += cc;
-        hacc += hh;
-      }
-    }
-    if constexpr (MULTI) {
-      // per (slot, length) statistics.  A frontier keeps each slot's paths together, so a
-      // warp accumulates a run of records with the same key in registers and only flushes
-      // (one set of atomics) when the key changes; lanes with a third key in the same
-      // record row are aggregated over the warp and flushed at once.
-#pragma unroll
-      for (int j = 0; j < P; ++j) {
-        const unsigned int key = mkey[j];
-        const bool v = key != 0xFFFFFFFFu;
-        const bool m0 = v && key == run.key;
-        if (m0) run.add(mcyc[j], mch[j], mh[j]);
-        const unsigned int rest = __ballot_sync(0xffffffffu, v && !m0);
-        if (rest) {
-          run.flush(p, s);
-          run.key = __shfl_sync(0xffffffffu, key, 31 - __clz(rest));
-          const bool m1 = v && !m0 && key == run.key;
-          if (m1) run.add(mcyc[j], mch[j], mh[j]);
-          unsigned int pending = __ballot_sync(0xffffffffu, v && !m0 && !m1);
-          while (pending) {
-            const int leader = __ffs(pending) - 1;
-            const unsigned int lk = __shfl_sync(0xffffffffu, key, leader);
-            const bool mine = key == lk;
-            const unsigned int grp = __ballot_sync(0xffffffffu, mine);
-            StatRun one;
-            one.key = lk;
-            if (mine) one.add(mcyc[j], mch[j], mh[j]);
-            one.flush(p, s);
-            pending &= ~grp;
+            hacc += mix64(H[j] + rtab[v] + (unsigned long long)(t + 1) * kGamma);
           }
         }
       }
@@ -470,27 +447,12 @@ __device__ __forceinline__ void process_bitset(const EngineParams& p, const Step
 #pragma unroll
           for (int k = 0; k < W; ++k) any |= ch[j][k];
           if (!any) continue;
-          unsigned int v1, vt, tt = t, Lr = L, mhi = 0;
-          unsigned long long go = 0;
-          if constexpr (MULTI) {
-            v1 = M[j] & 63u;
-            vt = (M[j] >> 6) & 63u;
-            tt = (M[j] >> 12) & 63u;
-            const unsigned int g = M[j] >> 18;
-            go = (unsigned long long)g * 64ull;
-            Lr = __ldg(p.Lg + g);
-            mhi = v1 | ((tt + 1) << 12) | (g << 18);
-          } else {
-            v1 = M[j] & 0xFFFFu;
-            vt = M[j] >> 16;
-            mhi = v1;
-          }
-          const bool next_ok = MULTI ? (tt + 2 < Lr) : next_ok1;
+          const unsigned int v1 = M[j] & 0xFFFFu, vt = M[j] >> 16;
           unsigned long long nb[W], a1[W];
 #pragma unroll
           for (int k = 0; k < W; ++k) {
-            nb[k] = B[j][k] | (MULTI ? __ldg(adj + go + vt) : adj[(unsigned long long)vt * W + k]);
-            a1[k] = MULTI ? __ldg(adj + go + v1) : adj[(unsigned long long)v1 * W + k];
+            nb[k] = B[j][k] | adj[(unsigned long long)vt * W + k];
+            a1[k] = adj[(unsigned long long)v1 * W + k];
           }
 #pragma unroll
           for (int k = 0; k < W; ++k) {
@@ -501,15 +463,11 @@ __device__ __forceinline__ void process_bitset(const EngineParams& p, const Step
               if (slot < ds) {
 #pragma unroll
                 for (int q = 0; q < W; ++q) dB[q * ds + slot] = nb[q];
-                dH[slot] = H[j] + (MULTI ? __ldg(rtab + go + v) : rtab[v]);
-                dM[slot] = MULTI ? (mhi | (v << 6)) : (mhi | (v << 16));
+                dH[slot] = H[j] + rtab[v];
+                dM[slot] = v1 | (v << 16);
                 if (next_ok) {
 #pragma unroll
-                  for (int q = 0; q < W; ++q) {
-                    const unsigned long long av =
-                        MULTI ? __ldg(adj + go + v) : adj[(unsigned long long)v * W + q];
-                    nx += __popcll(av & ~nb[q] & ~a1[q]);
-                  }
+                  for (int q = 0; q < W; ++q) nx += __popcll(adj[(unsigned long long)v * W + q] & ~nb[q] & ~a1[q]);
                 }
               } else {
                 set_err(p.ctl, kDevBounds, 1);
@@ -521,12 +479,11 @@ __device__ __forceinline__ void process_bitset(const EngineParams& p, const Step
       }
     }
   }
-  if constexpr (MULTI) run.flush(p, s);
   block_sum3_u64(nx, ncyc, hacc, s_red);
   if (tid == 0) {
     if (nx) atomicAdd(&nxtp[s % 3], nx);
-    if (!MULTI && ncyc) atomicAdd(&p.hist[t + 1], ncyc);
-    if (!MULTI && hacc) atomicAdd(p.hash, hacc);
+    if (ncyc) atomicAdd(&p.hist[t + 1], ncyc);
+    if (hacc) atomicAdd(p.hash, hacc);
   }
 }
 
@@ -1052,11 +1009,15 @@ __device__ __forceinline__ void process_bitset_fused(const EngineParams& p, cons
   }
 }
 
-// The batch form of the flattened expansion (records of many graphs in one frontier; M
-// holds v1, vt, t and the graph's slot g, whose rows and r-table sit at g * 64).  Per-path
-// statistics (paths expanded, children and closings per (slot, length)) are accumulated
-// in lane order as runs of one key, as in the per-lane form; a closing's hash is added to
-// its slot's sum by one atomic per distinct slot among the lanes of a round.
+// The batch form of the flattened expansion: records of many graphs in one frontier (the
+// slot g in M names the graph, whose rows and r-table sit at g * 64).  A stored record
+// carries its children C (Adj(vt) & ~B & ~Adj(v1), found when the path was created), so
+// expanding it needs no adjacency of its own: each child <p, w> is listed as an entry and,
+// one entry per lane, gets its candidates Adj(w) & ~N; those adjacent to v1 close cycles of
+// t + 2 vertices, which are hashed at once, and the rest are the child's own children.  A
+// child with no children of its own is counted (tcount) but not stored.  One slot atomic
+// per list of entries, issued between the pass that finds the stored children and the pass
+// that writes them.
 //
 // Work distribution: a warp takes contiguous chunks of the step's records from a step
 // counter (one atomic per chunk), so its rounds mostly stay inside one graph's run of
@@ -1067,29 +1028,33 @@ template <int NT>
 __device__ __forceinline__ void process_multi_flat(const EngineParams& p, const StepPlan& pl,
                                                    const unsigned long long* adj, const unsigned long long* rtab) {
   constexpr int P = KindTraits<Kind::Multi>::P;
-  constexpr unsigned int CL = FlatSmem<1, P, NT>::CL;
+  constexpr unsigned int CL = FlatSmem<1, P, NT>::CL;  // entries per list (a multiple of 32)
+  constexpr int KL = CL / 32;                           // entries per lane per list
   __shared__ FlatSmem<1, P, NT> fs;
   __shared__ unsigned long long s_gadj[NT / 32][64];
   __shared__ unsigned long long s_grt[NT / 32][64];
   const unsigned int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  unsigned long long* snb = fs.nb[wid];
-  unsigned long long* sh = fs.h[wid];
-  unsigned int* smeta = fs.v1[wid];  // v1 | t << 6 | g << 12 | (t + 2 < L'_g) << 31
+  unsigned long long* snb = fs.nb[wid];  // N of each staged record
+  unsigned long long* sh = fs.h[wid];    // H
+  // v1 | t << 6 | g << 12 | (t + 2 <= L'_g) << 30 | (t + 2 < L'_g) << 31
+  unsigned int* smeta = fs.v1[wid];
   unsigned int* sl = fs.list[wid];
   unsigned long long* ga = s_gadj[wid];
   unsigned long long* gr = s_grt[wid];
   const unsigned long long ss = pl.src_stride, ds = pl.dst_stride;
-  const unsigned long long* sB = reinterpret_cast<const unsigned long long*>(p.arena + pl.src_base);
-  const unsigned long long* sH = sB + ss;
+  const unsigned long long* sN = reinterpret_cast<const unsigned long long*>(p.arena + pl.src_base);
+  const unsigned long long* sC = sN + ss;
+  const unsigned long long* sH = sC + ss;
   const unsigned int* sM = reinterpret_cast<const unsigned int*>(sH + ss);
-  unsigned long long* dB = reinterpret_cast<unsigned long long*>(p.arena + pl.dst_base);
-  unsigned long long* dH = dB + ds;
+  unsigned long long* dN = reinterpret_cast<unsigned long long*>(p.arena + pl.dst_base);
+  unsigned long long* dC = dN + ds;
+  unsigned long long* dH = dC + ds;
   unsigned int* dM = reinterpret_cast<unsigned int*>(dH + ds);
-  const bool store = ds != 0;
   const unsigned long long s = pl.s;
+  const unsigned int lt_mask = (1u << lane) - 1u;
   unsigned long long nx = 0;
-  StatRun run;
-  run.key = 0xFFFFFFFFu;
+  StatRun prun, crun;  // the records expanded; the children created
+  prun.key = crun.key = 0xFFFFFFFFu;
   unsigned int cg = 0xFFFFFFFFu;  // graph staged in ga / gr
   unsigned int cL = 0;            // its L'
   auto A = [&](unsigned int g, unsigned int v) -> unsigned long long {
@@ -1099,83 +1064,80 @@ __device__ __forceinline__ void process_multi_flat(const EngineParams& p, const 
     return g == cg ? gr[v] : __ldg(rtab + (unsigned long long)g * 64ull + v);
   };
 
-  // children entries [0, n) take slots base + [0, n)
-  auto flush_children = [&](unsigned int n, unsigned long long base) {
+  // the children listed in sl[0, n): entry i = (staged record << 8 | w)
+  auto flush_children = [&](unsigned int n) {
     __syncwarp();
-    base = __shfl_sync(0xffffffffu, base, 0);
-    for (unsigned int i = lane; i < n; i += 32) {
-      const unsigned int e = sl[i], pj = e >> 8, v = e & 0xFFu;
-      const unsigned int meta = smeta[pj], v1 = meta & 63u, tt = (meta >> 6) & 63u, g = (meta >> 12) & 0x7FFFFu;
-      const unsigned long long slot = base + i;
-      if (slot < ds) {
-        const unsigned long long nb = snb[pj];
-        dB[slot] = nb;
-        dH[slot] = sh[pj] + R(g, v);
-        dM[slot] = v1 | (v << 6) | ((tt + 1) << 12) | (g << 18);
-        if (meta >> 31) nx += __popcll(A(g, v) & ~nb & ~A(g, v1));
-      } else {
-        set_err(p.ctl, kDevBounds, 1);
-      }
-    }
-    __syncwarp();
-  };
-  auto flush_closings = [&](unsigned int n) {
-    __syncwarp();
-    for (unsigned int r0 = 0; r0 < n; r0 += 32) {
-      const unsigned int i = r0 + lane;
-      unsigned int g = 0xFFFFFFFFu;
-      unsigned long long h = 0;
+    // pass 1: which children are stored (they have children of their own)
+    unsigned int sb[KL];
+    unsigned int tot = 0;
+#pragma unroll
+    for (int k = 0; k < KL; ++k) {
+      const unsigned int i = k * 32 + lane;
+      bool stv = false;
       if (i < n) {
-        const unsigned int e = sl[i], pj = e >> 8, v = e & 0xFFu;
-        const unsigned int meta = smeta[pj], tt = (meta >> 6) & 63u;
-        g = (meta >> 12) & 0x7FFFFu;
-        h = mix64(sh[pj] + R(g, v) + (unsigned long long)(tt + 1) * kGamma);
+        const unsigned int e = sl[i], pj = e >> 8, w = e & 0xFFu;
+        const unsigned int meta = smeta[pj], g = (meta >> 12) & 0x3FFFu;
+        if (meta >> 31) stv = (A(g, w) & ~snb[pj] & ~A(g, meta & 63u)) != 0ull;
       }
-      // usually every active lane of a round closes cycles of one slot (one warp sum,
-      // one atomic); otherwise per lane
-      const unsigned int g0 = __shfl_sync(0xffffffffu, g, 0);  // lane 0 is active (n > r0)
-      if (__all_sync(0xffffffffu, g == g0 || i >= n)) {
-        const unsigned long long sum = warp_sum_u64(h);
-        if (lane == 0) atomicAdd(&p.hash[g0], sum);
-      } else if (i < n) {
-        atomicAdd(&p.hash[g], h);
-      }
+      sb[k] = __ballot_sync(0xffffffffu, stv);
+      tot += __popc(sb[k]);
     }
-    __syncwarp();
-  };
-  unsigned long long m[P];
-  auto list_and_work = [&](bool children) {
-    unsigned int cnt = 0;
-#pragma unroll
-    for (int j = 0; j < P; ++j) cnt += __popcll(m[j]);
-    unsigned int incl = cnt;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const unsigned int y = __shfl_up_sync(0xffffffffu, incl, o);
-      if (lane >= (unsigned)o) incl += y;
-    }
-    const unsigned int excl = incl - cnt, total = __shfl_sync(0xffffffffu, incl, 31);
-    // a child list's slots: one atomic, issued before the listing so that its round trip
-    // overlaps it
     unsigned long long base = 0;
-    if (children && total && lane == 0) base = atomicAdd(&p.ctl->cnt[s % 3], (unsigned long long)total);
-    for (unsigned int c0 = 0; c0 < total; c0 += CL) {
-      if (cnt && excl < c0 + CL && excl + cnt > c0) {
-        unsigned int idx = excl;
+    if (lane == 0 && tot) base = atomicAdd(&p.ctl->cnt[s % 3], (unsigned long long)tot);
+    // pass 2 (while the atomic is in flight): closings of each child, hashed at once, and
+    // the statistics
 #pragma unroll
-        for (int j = 0; j < P; ++j) {
-          unsigned long long b = m[j];
-          while (b) {
-            const unsigned int v = __ffsll((long long)b) - 1;
-            b &= b - 1;
-            if (idx >= c0 && idx < c0 + CL) sl[idx - c0] = (unsigned int)(j * 32 + lane) << 8 | v;
-            ++idx;
+    for (int k = 0; k < KL; ++k) {
+      const unsigned int i = k * 32 + lane;
+      unsigned int key = 0xFFFFFFFFu, nc = 0, st = 0;
+      unsigned long long hs = 0;
+      if (i < n) {
+        const unsigned int e = sl[i], pj = e >> 8, w = e & 0xFFu;
+        const unsigned int meta = smeta[pj], tc = ((meta >> 6) & 63u) + 1u, g = (meta >> 12) & 0x3FFFu;
+        const unsigned long long aw = A(g, w), a1 = A(g, meta & 63u);
+        const unsigned long long cand = aw & ~snb[pj];
+        if (meta & 0x40000000u) {  // cycles of tc + 1 vertices
+          unsigned long long close = cand & a1;
+          nc = __popcll(close);
+          const unsigned long long hc = sh[pj] + R(g, w), gam = (unsigned long long)(tc + 1) * kGamma;
+          while (close) {
+            const unsigned int x = __ffsll((long long)close) - 1;
+            close &= close - 1;
+            hs += mix64(hc + R(g, x) + gam);
           }
         }
+        if ((sb[k] >> lane) & 1u) {
+          st = 1;
+          nx += __popcll(cand & ~a1);
+        }
+        key = g << 6 | tc;
       }
-      if (children) flush_children(min(CL, total - c0), base + c0);
-      else flush_closings(min(CL, total - c0));
+      account(crun, p, s, key, 0u, 0u, nc, st, hs);
     }
+    // pass 3: the stored children's records, at base + stored entries before them
+    const unsigned long long b0 = __shfl_sync(0xffffffffu, base, 0);
+    unsigned int pre = 0;
+#pragma unroll
+    for (int k = 0; k < KL; ++k) {
+      const unsigned int i = k * 32 + lane;
+      if ((sb[k] >> lane) & 1u) {
+        const unsigned int e = sl[i], pj = e >> 8, w = e & 0xFFu;
+        const unsigned int meta = smeta[pj], v1 = meta & 63u, tc = ((meta >> 6) & 63u) + 1u,
+                           g = (meta >> 12) & 0x3FFFu;
+        const unsigned long long aw = A(g, w), a1 = A(g, v1), np = snb[pj];
+        const unsigned long long slot = b0 + pre + __popc(sb[k] & lt_mask);
+        if (slot < ds) {
+          dN[slot] = np | aw;
+          dC[slot] = aw & ~np & ~a1;
+          dH[slot] = sh[pj] + R(g, w);
+          dM[slot] = v1 | (tc << 12) | (g << 18);
+        } else {
+          set_err(p.ctl, kDevBounds, 1);
+        }
+      }
+      pre += __popc(sb[k]);
+    }
+    __syncwarp();
   };
 
   const unsigned int pf = p.pf >= 1 && p.pf <= (unsigned)P ? p.pf : (unsigned)P;
@@ -1192,10 +1154,21 @@ __device__ __forceinline__ void process_multi_flat(const EngineParams& p, const 
     if (c0 >= total) break;
     const unsigned long long cend = pl.begin + min(c0 + chunk, total);
     for (unsigned long long wb = pl.begin + c0; wb < cend; wb += RW) {
+      const unsigned long long t0 = wb + lane;
+      unsigned long long N[P], C[P], H[P];
+      unsigned int M[P];
+#pragma unroll
+      for (int j = 0; j < P; ++j) {
+        const unsigned long long i = t0 + (unsigned long long)j * 32ull;
+        const bool valid = (unsigned)j < pf && i < cend;
+        N[j] = valid ? ldcg64(sN + i) : 0ull;
+        C[j] = valid ? ldcg64(sC + i) : 0ull;
+        H[j] = valid ? ldcg64(sH + i) : 0ull;
+        M[j] = valid ? ldcg32(sM + i) : 0xFFFFFFFFu;
+      }
       // the graph of the round's first record (always valid): stage it if it changed
-      const unsigned int g0 = ldcg32(sM + wb) >> 18;
+      const unsigned int g0 = __shfl_sync(0xffffffffu, M[0], 0) >> 18;
       if (g0 != cg) {
-        __syncwarp();
         ga[lane] = __ldg(adj + (unsigned long long)g0 * 64ull + lane);
         ga[lane + 32] = __ldg(adj + (unsigned long long)g0 * 64ull + lane + 32);
         gr[lane] = __ldg(rtab + (unsigned long long)g0 * 64ull + lane);
@@ -1204,66 +1177,49 @@ __device__ __forceinline__ void process_multi_flat(const EngineParams& p, const 
         cg = g0;
         __syncwarp();
       }
-      const unsigned long long t0 = wb + lane;
-      unsigned long long ch[P];
-      unsigned int key[P], nc[P], nk[P];
 #pragma unroll
       for (int j = 0; j < P; ++j) {
-        const unsigned long long i = t0 + (unsigned long long)j * 32ull;
-        const bool valid = (unsigned)j < pf && i < cend;
-        const unsigned long long B = valid ? ldcg64(sB + i) : ~0ull;
-        const unsigned long long H = valid ? ldcg64(sH + i) : 0ull;
-        const unsigned int M = valid ? ldcg32(sM + i) : 0u;
-        const unsigned int v1 = M & 63u, vt = (M >> 6) & 63u, tt = (M >> 12) & 63u, g = M >> 18;
+        const bool valid = M[j] != 0xFFFFFFFFu;
+        const unsigned int v1 = M[j] & 63u, tt = (M[j] >> 12) & 63u, g = M[j] >> 18;
         const unsigned int Lr = valid ? (g == cg ? cL : p.Lg[g]) : 0u;
-        const unsigned long long at = A(g, vt), a1 = A(g, v1);
-        const unsigned long long cand = at & ~B;
-        m[j] = (tt + 1 <= Lr) ? (cand & a1) : 0ull;
-        ch[j] = (store && tt + 1 < Lr) ? (cand & ~a1) : 0ull;
         const unsigned int pj = j * 32 + lane;
-        snb[pj] = B | at;
-        sh[pj] = H;
-        smeta[pj] = v1 | (tt << 6) | (g << 12) | ((tt + 2 < Lr) ? 0x80000000u : 0u);
-        key[j] = valid ? (g << 6 | tt) : 0xFFFFFFFFu;
-        nc[j] = __popcll(m[j]);
-        nk[j] = __popcll(ch[j]);
+        snb[pj] = N[j];
+        sh[pj] = H[j];
+        smeta[pj] = v1 | (tt << 6) | (g << 12) | ((tt + 2 <= Lr) ? 0x40000000u : 0u) |
+                    ((tt + 2 < Lr) ? 0x80000000u : 0u);
+        account(prun, p, s, valid ? (g << 6 | tt) : 0xFFFFFFFFu, valid ? 1u : 0u, __popcll(C[j]), 0u, 0u, 0ull);
       }
-      // per (slot, length) counts, as runs of one key (no hash here: closings add theirs)
+      // list the children (path, w) and work them off CL at a time
+      unsigned int cnt = 0;
 #pragma unroll
-      for (int j = 0; j < P; ++j) {
-        const unsigned int k = key[j];
-        const bool v = k != 0xFFFFFFFFu;
-        const bool m0 = v && k == run.key;
-        if (m0) run.add(nc[j], nk[j], 0ull);
-        const unsigned int rest = __ballot_sync(0xffffffffu, v && !m0);
-        if (rest) {
-          run.flush(p, s);
-          run.key = __shfl_sync(0xffffffffu, k, 31 - __clz(rest));
-          const bool m1 = v && !m0 && k == run.key;
-          if (m1) run.add(nc[j], nk[j], 0ull);
-          unsigned int pending = __ballot_sync(0xffffffffu, v && !m0 && !m1);
-          while (pending) {
-            const int leader = __ffs(pending) - 1;
-            const unsigned int lk = __shfl_sync(0xffffffffu, k, leader);
-            const bool mine = k == lk;
-            const unsigned int grp = __ballot_sync(0xffffffffu, mine);
-            StatRun one;
-            one.key = lk;
-            if (mine) one.add(nc[j], nk[j], 0ull);
-            one.flush(p, s);
-            pending &= ~grp;
+      for (int j = 0; j < P; ++j) cnt += __popcll(C[j]);
+      unsigned int incl = cnt;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const unsigned int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= (unsigned)o) incl += y;
+      }
+      const unsigned int excl = incl - cnt, ctot = __shfl_sync(0xffffffffu, incl, 31);
+      for (unsigned int l0 = 0; l0 < ctot; l0 += CL) {
+        if (cnt && excl < l0 + CL && excl + cnt > l0) {
+          unsigned int idx = excl;
+#pragma unroll
+          for (int j = 0; j < P; ++j) {
+            unsigned long long b = C[j];
+            while (b) {
+              const unsigned int w = __ffsll((long long)b) - 1;
+              b &= b - 1;
+              if (idx >= l0 && idx < l0 + CL) sl[idx - l0] = (unsigned int)(j * 32 + lane) << 8 | w;
+              ++idx;
+            }
           }
         }
-      }
-      list_and_work(false);
-      if (store) {
-#pragma unroll
-        for (int j = 0; j < P; ++j) m[j] = ch[j];
-        list_and_work(true);
+        flush_children(min(CL, ctot - l0));
       }
     }
   }
-  run.flush(p, s);
+  prun.flush(p, s);
+  crun.flush(p, s);
   const unsigned long long tot = warp_sum_u64(nx);
   if (lane == 0 && tot) atomicAdd(&p.ctl->nxt[s % 3], tot);
 }
