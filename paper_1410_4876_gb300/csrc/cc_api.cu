@@ -780,7 +780,12 @@ static cc_status batch_run(cc_batch_set* bs, uint32_t max_len, cc_batch_id* out)
   p.frames = c->frames;
   p.max_depth = c->frames_cap;
   p.n = 64;
-  p.L = 64;
+  // the deepest stored level of any graph bounds the levels a depth-first chunk must leave
+  // room for (each graph's own L' is in Lg)
+  unsigned int maxL = 3;
+  for (unsigned int g = 0; g < count; ++g)
+    maxL = std::max(maxL, (max_len == 0 || max_len > bs->n[g]) ? bs->n[g] : max_len);
+  p.L = maxL;
   p.maxch = bs->maxch;
   p.adj = reinterpret_cast<unsigned long long*>(base + o_adj);
   p.rtab = reinterpret_cast<unsigned long long*>(base + o_rtab);

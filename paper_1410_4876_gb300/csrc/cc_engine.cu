@@ -1014,10 +1014,15 @@ __device__ __forceinline__ void process_bitset_fused(const EngineParams& p, cons
 // carries its children C (Adj(vt) & ~B & ~Adj(v1), found when the path was created), so
 // expanding it needs no adjacency of its own: each child <p, w> is listed as an entry and,
 // one entry per lane, gets its candidates Adj(w) & ~N; those adjacent to v1 close cycles of
-// t + 2 vertices, which are hashed at once, and the rest are the child's own children.  A
-// child with no children of its own is counted (tcount) but not stored.  One slot atomic
-// per list of entries, issued between the pass that finds the stored children and the pass
-// that writes them.
+// t + 2 vertices, which are hashed at once, and the rest are the child's own children.
+//
+// Slots: the children of a round of records are known before they are listed (the popcount
+// of C), so the round takes that many slots with one atomic, issued before the listing, and
+// its round trip overlaps the listing and the children's work.  A child with children of
+// its own is written at the next slot of the range; the range's last slots, one per child
+// without children, get C = 0 and no other field: an empty slot, which the next step skips
+// after reading C.  (Every child is counted in tcount; only the paths with children are
+// expanded again.)
 //
 // Work distribution: a warp takes contiguous chunks of the step's records from a step
 // counter (one atomic per chunk), so its rounds mostly stay inside one graph's run of
@@ -1064,80 +1069,57 @@ __device__ __forceinline__ void process_multi_flat(const EngineParams& p, const 
     return g == cg ? gr[v] : __ldg(rtab + (unsigned long long)g * 64ull + v);
   };
 
-  // the children listed in sl[0, n): entry i = (staged record << 8 | w)
-  auto flush_children = [&](unsigned int n) {
+  // the children listed in sl[0, n) (entry = staged record << 8 | w); those with children
+  // of their own are written from slot `next` on.  Returns how many were written.
+  auto flush_children = [&](unsigned int n, unsigned long long next) -> unsigned int {
     __syncwarp();
-    // pass 1: which children are stored (they have children of their own)
-    unsigned int sb[KL];
-    unsigned int tot = 0;
+    unsigned int pre = 0;
 #pragma unroll
     for (int k = 0; k < KL; ++k) {
       const unsigned int i = k * 32 + lane;
-      bool stv = false;
+      unsigned int key = 0xFFFFFFFFu, nc = 0;
+      unsigned long long hs = 0, chc = 0, nw = 0, hc = 0;
+      unsigned int mw = 0;
       if (i < n) {
         const unsigned int e = sl[i], pj = e >> 8, w = e & 0xFFu;
-        const unsigned int meta = smeta[pj], g = (meta >> 12) & 0x3FFFu;
-        if (meta >> 31) stv = (A(g, w) & ~snb[pj] & ~A(g, meta & 63u)) != 0ull;
-      }
-      sb[k] = __ballot_sync(0xffffffffu, stv);
-      tot += __popc(sb[k]);
-    }
-    unsigned long long base = 0;
-    if (lane == 0 && tot) base = atomicAdd(&p.ctl->cnt[s % 3], (unsigned long long)tot);
-    // pass 2 (while the atomic is in flight): closings of each child, hashed at once, and
-    // the statistics
-#pragma unroll
-    for (int k = 0; k < KL; ++k) {
-      const unsigned int i = k * 32 + lane;
-      unsigned int key = 0xFFFFFFFFu, nc = 0, st = 0;
-      unsigned long long hs = 0;
-      if (i < n) {
-        const unsigned int e = sl[i], pj = e >> 8, w = e & 0xFFu;
-        const unsigned int meta = smeta[pj], tc = ((meta >> 6) & 63u) + 1u, g = (meta >> 12) & 0x3FFFu;
-        const unsigned long long aw = A(g, w), a1 = A(g, meta & 63u);
-        const unsigned long long cand = aw & ~snb[pj];
+        const unsigned int meta = smeta[pj], v1 = meta & 63u, tc = ((meta >> 6) & 63u) + 1u,
+                           g = (meta >> 12) & 0x3FFFu;
+        const unsigned long long aw = A(g, w), a1 = A(g, v1), np = snb[pj];
+        const unsigned long long cand = aw & ~np;
+        hc = sh[pj] + R(g, w);
         if (meta & 0x40000000u) {  // cycles of tc + 1 vertices
           unsigned long long close = cand & a1;
           nc = __popcll(close);
-          const unsigned long long hc = sh[pj] + R(g, w), gam = (unsigned long long)(tc + 1) * kGamma;
+          const unsigned long long gam = (unsigned long long)(tc + 1) * kGamma;
           while (close) {
             const unsigned int x = __ffsll((long long)close) - 1;
             close &= close - 1;
             hs += mix64(hc + R(g, x) + gam);
           }
         }
-        if ((sb[k] >> lane) & 1u) {
-          st = 1;
-          nx += __popcll(cand & ~a1);
-        }
+        chc = (meta >> 31) ? (cand & ~a1) : 0ull;
+        nw = np | aw;
+        mw = v1 | (tc << 12) | (g << 18);
         key = g << 6 | tc;
       }
-      account(crun, p, s, key, 0u, 0u, nc, st, hs);
-    }
-    // pass 3: the stored children's records, at base + stored entries before them
-    const unsigned long long b0 = __shfl_sync(0xffffffffu, base, 0);
-    unsigned int pre = 0;
-#pragma unroll
-    for (int k = 0; k < KL; ++k) {
-      const unsigned int i = k * 32 + lane;
-      if ((sb[k] >> lane) & 1u) {
-        const unsigned int e = sl[i], pj = e >> 8, w = e & 0xFFu;
-        const unsigned int meta = smeta[pj], v1 = meta & 63u, tc = ((meta >> 6) & 63u) + 1u,
-                           g = (meta >> 12) & 0x3FFFu;
-        const unsigned long long aw = A(g, w), a1 = A(g, v1), np = snb[pj];
-        const unsigned long long slot = b0 + pre + __popc(sb[k] & lt_mask);
+      const unsigned int b = __ballot_sync(0xffffffffu, chc != 0ull);
+      if (chc) {
+        const unsigned long long slot = next + pre + __popc(b & lt_mask);
         if (slot < ds) {
-          dN[slot] = np | aw;
-          dC[slot] = aw & ~np & ~a1;
-          dH[slot] = sh[pj] + R(g, w);
-          dM[slot] = v1 | (tc << 12) | (g << 18);
+          dN[slot] = nw;
+          dC[slot] = chc;
+          dH[slot] = hc;
+          dM[slot] = mw;
+          nx += __popcll(chc);
         } else {
           set_err(p.ctl, kDevBounds, 1);
         }
       }
-      pre += __popc(sb[k]);
+      pre += __popc(b);
+      account(crun, p, s, key, 0u, 0u, nc, chc ? 1u : 0u, hs);
     }
     __syncwarp();
+    return pre;
   };
 
   const unsigned int pf = p.pf >= 1 && p.pf <= (unsigned)P ? p.pf : (unsigned)P;
@@ -1160,14 +1142,33 @@ __device__ __forceinline__ void process_multi_flat(const EngineParams& p, const 
 #pragma unroll
       for (int j = 0; j < P; ++j) {
         const unsigned long long i = t0 + (unsigned long long)j * 32ull;
-        const bool valid = (unsigned)j < pf && i < cend;
+        C[j] = ((unsigned)j < pf && i < cend) ? ldcg64(sC + i) : 0ull;
+        const bool valid = C[j] != 0ull;  // (C = 0: an empty slot)
         N[j] = valid ? ldcg64(sN + i) : 0ull;
-        C[j] = valid ? ldcg64(sC + i) : 0ull;
         H[j] = valid ? ldcg64(sH + i) : 0ull;
         M[j] = valid ? ldcg32(sM + i) : 0xFFFFFFFFu;
       }
-      // the graph of the round's first record (always valid): stage it if it changed
-      const unsigned int g0 = __shfl_sync(0xffffffffu, M[0], 0) >> 18;
+      // the round's children and their slots (one atomic, in flight during the listing)
+      unsigned int cnt = 0;
+#pragma unroll
+      for (int j = 0; j < P; ++j) cnt += __popcll(C[j]);
+      unsigned int incl = cnt;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const unsigned int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= (unsigned)o) incl += y;
+      }
+      const unsigned int excl = incl - cnt, ctot = __shfl_sync(0xffffffffu, incl, 31);
+      if (ctot == 0) continue;  // a round of empty slots only
+      unsigned long long base = 0;
+      if (lane == 0) base = atomicAdd(&p.ctl->cnt[s % 3], (unsigned long long)ctot);
+      // the graph of the round's first record (there is one: ctot > 0): stage it if it changed
+      unsigned int g0 = 0xFFFFFFFFu;
+#pragma unroll
+      for (int j = 0; j < P; ++j) {
+        const unsigned int bal = __ballot_sync(0xffffffffu, M[j] != 0xFFFFFFFFu);
+        if (g0 == 0xFFFFFFFFu && bal) g0 = __shfl_sync(0xffffffffu, M[j], __ffs(bal) - 1) >> 18;
+      }
       if (g0 != cg) {
         ga[lane] = __ldg(adj + (unsigned long long)g0 * 64ull + lane);
         ga[lane + 32] = __ldg(adj + (unsigned long long)g0 * 64ull + lane + 32);
@@ -1190,16 +1191,8 @@ __device__ __forceinline__ void process_multi_flat(const EngineParams& p, const 
         account(prun, p, s, valid ? (g << 6 | tt) : 0xFFFFFFFFu, valid ? 1u : 0u, __popcll(C[j]), 0u, 0u, 0ull);
       }
       // list the children (path, w) and work them off CL at a time
-      unsigned int cnt = 0;
-#pragma unroll
-      for (int j = 0; j < P; ++j) cnt += __popcll(C[j]);
-      unsigned int incl = cnt;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const unsigned int y = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= (unsigned)o) incl += y;
-      }
-      const unsigned int excl = incl - cnt, ctot = __shfl_sync(0xffffffffu, incl, 31);
+      base = __shfl_sync(0xffffffffu, base, 0);
+      unsigned long long next = base;
       for (unsigned int l0 = 0; l0 < ctot; l0 += CL) {
         if (cnt && excl < l0 + CL && excl + cnt > l0) {
           unsigned int idx = excl;
@@ -1214,7 +1207,11 @@ __device__ __forceinline__ void process_multi_flat(const EngineParams& p, const 
             }
           }
         }
-        flush_children(min(CL, ctot - l0));
+        next += flush_children(min(CL, ctot - l0), next);
+      }
+      // the range's remaining slots (children without children): empty
+      for (unsigned long long q = next + lane; q < base + ctot; q += 32) {
+        if (q < ds) dC[q] = 0ull;
       }
     }
   }
