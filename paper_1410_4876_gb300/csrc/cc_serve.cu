@@ -32,6 +32,7 @@ struct Request {
   std::vector<uint32_t> rows, cols;
   uint64_t pred_bytes;
   uint64_t seed_bound;  // (max_degree - 1) * m / 2: bound on its initial triplets
+  uint32_t maxch;       // max_degree - 1 (at least 1): children per path at most
   Clock::time_point t_submit;
 };
 
@@ -39,6 +40,7 @@ struct SlotState {
   bool busy = false;
   uint64_t id = 0;
   uint64_t pred_bytes = 0;
+  uint32_t maxch = 1, L = 3;  // the request's children-per-path bound and L
   Clock::time_point t_submit, t_admit;
 };
 
@@ -103,6 +105,10 @@ struct cc_server {
   EngineParams p{};
   int grid = 0, block = 256;
   bool launched = false;
+  // requests in flight by children-per-path bound and by L': the engine's chunk planning
+  // uses the largest of each (a frontier holds only paths of requests in flight)
+  unsigned int n_maxch[kMultiMaxN + 1] = {};
+  unsigned int n_L[kMultiMaxN + 1] = {};
 };
 
 // ------------------------------------------------------------------ prediction
@@ -256,6 +262,7 @@ extern "C" cc_status cc_serve_submit(cc_server* v, uint32_t n, const uint32_t* r
   const uint64_t m = row_ptr[n] / 2;
   r.pred_bytes = predicted_bytes ? predicted_bytes : cc_serve_predict_bytes(n, m, md);
   r.seed_bound = md > 1 ? (uint64_t)(md - 1) * m / 2 : 0;
+  r.maxch = md > 1 ? md - 1 : 1;
   r.t_submit = Clock::now();
   v->queue.push_back(std::move(r));
   *out_id = v->queue.back().id;
@@ -318,6 +325,8 @@ extern "C" cc_status cc_serve_step(cc_server* v, cc_completion* out, uint32_t ca
       cp.latency_us = std::chrono::duration<double, std::micro>(now - ss.t_submit).count();
       v->done.push_back(cp);
       v->pred_in_flight -= ss.pred_bytes;
+      v->n_maxch[ss.maxch] -= 1;
+      v->n_L[ss.L] -= 1;
       ss.busy = false;
       v->free_slots.push_back(sl);
       v->in_flight -= 1;
@@ -375,6 +384,10 @@ extern "C" cc_status cc_serve_step(cc_server* v, cc_completion* out, uint32_t ca
       ss.pred_bytes = r.pred_bytes;
       ss.t_submit = r.t_submit;
       ss.t_admit = now;
+      ss.maxch = r.maxch;
+      ss.L = std::max(3u, (v->o.max_len == 0 || v->o.max_len > r.n) ? r.n : v->o.max_len);
+      v->n_maxch[ss.maxch] += 1;
+      v->n_L[ss.L] += 1;
     }
     roff[na] = ro;
     coff[na] = co;
@@ -423,6 +436,13 @@ extern "C" cc_status cc_serve_step(cc_server* v, cc_completion* out, uint32_t ca
 
   // 3. expansion steps over the shared frontier
   if (ctl.depth > 0 || na) {
+    unsigned int mc = 1, mL = 4;
+    for (unsigned int i = kMultiMaxN; i > 0; --i)
+      if (v->n_maxch[i]) { mc = i; break; }
+    for (unsigned int i = kMultiMaxN; i > 3; --i)
+      if (v->n_L[i]) { mL = i; break; }
+    v->p.maxch = mc;
+    v->p.L = mL;
     ok(launch_engine(Kind::Multi, v->p, v->grid, v->block, 0, stm));
     v->launched = true;
   }
