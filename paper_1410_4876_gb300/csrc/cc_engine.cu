@@ -93,13 +93,11 @@ struct KindTraits {
 template <Kind K>
 __device__ __forceinline__ unsigned long long region_bytes(unsigned long long stride, unsigned int t_child) {
   if constexpr (KindTraits<K>::csr) return csr_region_bytes(stride, t_child);
-  else if constexpr (KindTraits<K>::multi) return multi_region_bytes(stride);
   else return bitset_region_bytes(stride, KindTraits<K>::W);
 }
 template <Kind K>
 __device__ __forceinline__ unsigned long long record_bytes(unsigned int t_child) {
   if constexpr (KindTraits<K>::csr) return 2ull * csr_rec_u16(t_child);
-  else if constexpr (KindTraits<K>::multi) return 28ull;
   else return 8ull * KindTraits<K>::W + 12ull;
 }
 
@@ -293,77 +291,39 @@ __device__ void commit_step(const EngineParams& p, LocalState& st, unsigned long
 
 // ------------------------------------------------------------------ bitset expansion
 
-// Batch-mode statistics of one (slot, length tt) key, accumulated per lane; flush() is
-// warp-collective and adds the warp's sums with one lane's atomics:
-//   hist[tt + 1]   += c        cycles closed by paths of tt vertices
-//   tcount[tt + 1] += k        paths of tt + 1 vertices (children of paths of tt vertices)
-//   hash           += h
-//   live           += st - n   paths stored minus paths expanded (still in flight)
-//   last_step       = s + 1    when a path was expanded
+// Batch-mode statistics of one (slot, length) key, accumulated per lane; flush() is
+// warp-collective and adds the warp's sums to the slot's histogram, hash, stored-path
+// count and in-flight count with one lane's atomics.
 struct StatRun {
   unsigned int key;
-  unsigned int n = 0, k = 0, c = 0, st = 0;
+  unsigned int c = 0, k = 0, n = 0;
   unsigned long long h = 0;
-  __device__ __forceinline__ void add(unsigned int nn, unsigned int kk, unsigned int cc, unsigned int ss,
-                                      unsigned long long hh) {
-    n += nn;
-    k += kk;
+  __device__ __forceinline__ void add(unsigned int cc, unsigned int kk, unsigned long long hh) {
     c += cc;
-    st += ss;
+    k += kk;
+    n += 1;
     h += hh;
   }
   __device__ __forceinline__ void flush(const EngineParams& p, unsigned long long s) {
-    const unsigned int sn = __reduce_add_sync(0xffffffffu, n);
-    const unsigned int sk = __reduce_add_sync(0xffffffffu, k);
     const unsigned int sc = __reduce_add_sync(0xffffffffu, c);
-    const unsigned int sst = __reduce_add_sync(0xffffffffu, st);
+    const unsigned int sk = __reduce_add_sync(0xffffffffu, k);
+    const unsigned int sn = __reduce_add_sync(0xffffffffu, n);
     const unsigned long long sh = warp_sum_u64(h);
-    if ((threadIdx.x & 31) == 0 && key != 0xFFFFFFFFu) {
+    if ((threadIdx.x & 31) == 0 && key != 0xFFFFFFFFu && sn) {
       const unsigned int g = key >> 6, tt = key & 63u;
       const unsigned long long hb = (unsigned long long)g * kMultiHistStride;
       if (sc) atomicAdd(&p.hist[hb + tt + 1], (unsigned long long)sc);
       if (sh) atomicAdd(&p.hash[g], sh);
       if (sk) atomicAdd(&p.tcount[hb + tt + 1], (unsigned long long)sk);
-      if (p.live && sst != sn)
+      if (p.live)
         atomicAdd(reinterpret_cast<unsigned long long*>(&p.live[g]),
-                  (unsigned long long)((long long)sst - (long long)sn));
+                  (unsigned long long)((long long)sk - (long long)sn));
       if (p.last_step && sn) atomicMax(&p.last_step[g], (unsigned int)s + 1u);
     }
-    n = k = c = st = 0;
+    c = k = n = 0;
     h = 0;
   }
 };
-
-// Adds one value set per lane to the warp's run (lanes with key 0xFFFFFFFF add nothing).
-// Lanes whose key differs from the run's flush it and start a new run with the last such
-// lane's key; a third key in the same call is aggregated over its lanes and flushed at
-// once.  Warp-collective.
-__device__ __forceinline__ void account(StatRun& run, const EngineParams& p, unsigned long long s, unsigned int key,
-                                        unsigned int n, unsigned int k, unsigned int c, unsigned int st,
-                                        unsigned long long h) {
-  const bool v = key != 0xFFFFFFFFu;
-  const bool m0 = v && key == run.key;
-  if (m0) run.add(n, k, c, st, h);
-  const unsigned int rest = __ballot_sync(0xffffffffu, v && !m0);
-  if (rest) {
-    run.flush(p, s);
-    run.key = __shfl_sync(0xffffffffu, key, 31 - __clz(rest));
-    const bool m1 = v && !m0 && key == run.key;
-    if (m1) run.add(n, k, c, st, h);
-    unsigned int pending = __ballot_sync(0xffffffffu, v && !m0 && !m1);
-    while (pending) {
-      const int leader = __ffs(pending) - 1;
-      const unsigned int lk = __shfl_sync(0xffffffffu, key, leader);
-      const bool mine = key == lk;
-      const unsigned int grp = __ballot_sync(0xffffffffu, mine);
-      StatRun one;
-      one.key = lk;
-      if (mine) one.add(n, k, c, st, h);
-      one.flush(p, s);
-      pending &= ~grp;
-    }
-  }
-}
 
 // Algorithm 3 on bitset records.  For a path p = <v1 .. vt> with blocked set B:
 //   cand  = Adj(vt) & ~B      label test (l(v) > l(v2)), v not on p, chord test v2..v_{t-1}
@@ -1009,20 +969,11 @@ __device__ __forceinline__ void process_bitset_fused(const EngineParams& p, cons
   }
 }
 
-// The batch form of the flattened expansion: records of many graphs in one frontier (the
-// slot g in M names the graph, whose rows and r-table sit at g * 64).  A stored record
-// carries its children C (Adj(vt) & ~B & ~Adj(v1), found when the path was created), so
-// expanding it needs no adjacency of its own: each child <p, w> is listed as an entry and,
-// one entry per lane, gets its candidates Adj(w) & ~N; those adjacent to v1 close cycles of
-// t + 2 vertices, which are hashed at once, and the rest are the child's own children.
-//
-// Slots: the children of a round of records are known before they are listed (the popcount
-// of C), so the round takes that many slots with one atomic, issued before the listing, and
-// its round trip overlaps the listing and the children's work.  A child with children of
-// its own is written at the next slot of the range; the range's last slots, one per child
-// without children, get C = 0 and no other field: an empty slot, which the next step skips
-// after reading C.  (Every child is counted in tcount; only the paths with children are
-// expanded again.)
+// The batch form of the flattened expansion (records of many graphs in one frontier; M
+// holds v1, vt, t and the graph's slot g, whose rows and r-table sit at g * 64).  Per-path
+// statistics (paths expanded, children and closings per (slot, length)) are accumulated
+// in lane order as runs of one key, as in the per-lane form; a closing's hash is added to
+// its slot's sum by one atomic per distinct slot among the lanes of a round.
 //
 // Work distribution: a warp takes contiguous chunks of the step's records from a step
 // counter (one atomic per chunk), so its rounds mostly stay inside one graph's run of
@@ -1033,33 +984,29 @@ template <int NT>
 __device__ __forceinline__ void process_multi_flat(const EngineParams& p, const StepPlan& pl,
                                                    const unsigned long long* adj, const unsigned long long* rtab) {
   constexpr int P = KindTraits<Kind::Multi>::P;
-  constexpr unsigned int CL = FlatSmem<1, P, NT>::CL;  // entries per list (a multiple of 32)
-  constexpr int KL = CL / 32;                           // entries per lane per list
+  constexpr unsigned int CL = FlatSmem<1, P, NT>::CL;
   __shared__ FlatSmem<1, P, NT> fs;
   __shared__ unsigned long long s_gadj[NT / 32][64];
   __shared__ unsigned long long s_grt[NT / 32][64];
   const unsigned int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  unsigned long long* snb = fs.nb[wid];  // N of each staged record
-  unsigned long long* sh = fs.h[wid];    // H
-  // v1 | t << 6 | g << 12 | (t + 2 <= L'_g) << 30 | (t + 2 < L'_g) << 31
-  unsigned int* smeta = fs.v1[wid];
+  unsigned long long* snb = fs.nb[wid];
+  unsigned long long* sh = fs.h[wid];
+  unsigned int* smeta = fs.v1[wid];  // v1 | t << 6 | g << 12 | (t + 2 < L'_g) << 31
   unsigned int* sl = fs.list[wid];
   unsigned long long* ga = s_gadj[wid];
   unsigned long long* gr = s_grt[wid];
   const unsigned long long ss = pl.src_stride, ds = pl.dst_stride;
-  const unsigned long long* sN = reinterpret_cast<const unsigned long long*>(p.arena + pl.src_base);
-  const unsigned long long* sC = sN + ss;
-  const unsigned long long* sH = sC + ss;
+  const unsigned long long* sB = reinterpret_cast<const unsigned long long*>(p.arena + pl.src_base);
+  const unsigned long long* sH = sB + ss;
   const unsigned int* sM = reinterpret_cast<const unsigned int*>(sH + ss);
-  unsigned long long* dN = reinterpret_cast<unsigned long long*>(p.arena + pl.dst_base);
-  unsigned long long* dC = dN + ds;
-  unsigned long long* dH = dC + ds;
+  unsigned long long* dB = reinterpret_cast<unsigned long long*>(p.arena + pl.dst_base);
+  unsigned long long* dH = dB + ds;
   unsigned int* dM = reinterpret_cast<unsigned int*>(dH + ds);
+  const bool store = ds != 0;
   const unsigned long long s = pl.s;
-  const unsigned int lt_mask = (1u << lane) - 1u;
   unsigned long long nx = 0;
-  StatRun prun, crun;  // the records expanded; the children created
-  prun.key = crun.key = 0xFFFFFFFFu;
+  StatRun run;
+  run.key = 0xFFFFFFFFu;
   unsigned int cg = 0xFFFFFFFFu;  // graph staged in ga / gr
   unsigned int cL = 0;            // its L'
   auto A = [&](unsigned int g, unsigned int v) -> unsigned long long {
@@ -1069,57 +1016,83 @@ __device__ __forceinline__ void process_multi_flat(const EngineParams& p, const 
     return g == cg ? gr[v] : __ldg(rtab + (unsigned long long)g * 64ull + v);
   };
 
-  // the children listed in sl[0, n) (entry = staged record << 8 | w); those with children
-  // of their own are written from slot `next` on.  Returns how many were written.
-  auto flush_children = [&](unsigned int n, unsigned long long next) -> unsigned int {
+  // children entries [0, n) take slots base + [0, n)
+  auto flush_children = [&](unsigned int n, unsigned long long base) {
     __syncwarp();
-    unsigned int pre = 0;
-#pragma unroll
-    for (int k = 0; k < KL; ++k) {
-      const unsigned int i = k * 32 + lane;
-      unsigned int key = 0xFFFFFFFFu, nc = 0;
-      unsigned long long hs = 0, chc = 0, nw = 0, hc = 0;
-      unsigned int mw = 0;
-      if (i < n) {
-        const unsigned int e = sl[i], pj = e >> 8, w = e & 0xFFu;
-        const unsigned int meta = smeta[pj], v1 = meta & 63u, tc = ((meta >> 6) & 63u) + 1u,
-                           g = (meta >> 12) & 0x3FFFu;
-        const unsigned long long aw = A(g, w), a1 = A(g, v1), np = snb[pj];
-        const unsigned long long cand = aw & ~np;
-        hc = sh[pj] + R(g, w);
-        if (meta & 0x40000000u) {  // cycles of tc + 1 vertices
-          unsigned long long close = cand & a1;
-          nc = __popcll(close);
-          const unsigned long long gam = (unsigned long long)(tc + 1) * kGamma;
-          while (close) {
-            const unsigned int x = __ffsll((long long)close) - 1;
-            close &= close - 1;
-            hs += mix64(hc + R(g, x) + gam);
-          }
-        }
-        chc = (meta >> 31) ? (cand & ~a1) : 0ull;
-        nw = np | aw;
-        mw = v1 | (tc << 12) | (g << 18);
-        key = g << 6 | tc;
+    base = __shfl_sync(0xffffffffu, base, 0);
+    for (unsigned int i = lane; i < n; i += 32) {
+      const unsigned int e = sl[i], pj = e >> 8, v = e & 0xFFu;
+      const unsigned int meta = smeta[pj], v1 = meta & 63u, tt = (meta >> 6) & 63u, g = (meta >> 12) & 0x7FFFFu;
+      const unsigned long long slot = base + i;
+      if (slot < ds) {
+        const unsigned long long nb = snb[pj];
+        dB[slot] = nb;
+        dH[slot] = sh[pj] + R(g, v);
+        dM[slot] = v1 | (v << 6) | ((tt + 1) << 12) | (g << 18);
+        if (meta >> 31) nx += __popcll(A(g, v) & ~nb & ~A(g, v1));
+      } else {
+        set_err(p.ctl, kDevBounds, 1);
       }
-      const unsigned int b = __ballot_sync(0xffffffffu, chc != 0ull);
-      if (chc) {
-        const unsigned long long slot = next + pre + __popc(b & lt_mask);
-        if (slot < ds) {
-          dN[slot] = nw;
-          dC[slot] = chc;
-          dH[slot] = hc;
-          dM[slot] = mw;
-          nx += __popcll(chc);
-        } else {
-          set_err(p.ctl, kDevBounds, 1);
-        }
-      }
-      pre += __popc(b);
-      account(crun, p, s, key, 0u, 0u, nc, chc ? 1u : 0u, hs);
     }
     __syncwarp();
-    return pre;
+  };
+  auto flush_closings = [&](unsigned int n) {
+    __syncwarp();
+    for (unsigned int r0 = 0; r0 < n; r0 += 32) {
+      const unsigned int i = r0 + lane;
+      unsigned int g = 0xFFFFFFFFu;
+      unsigned long long h = 0;
+      if (i < n) {
+        const unsigned int e = sl[i], pj = e >> 8, v = e & 0xFFu;
+        const unsigned int meta = smeta[pj], tt = (meta >> 6) & 63u;
+        g = (meta >> 12) & 0x7FFFFu;
+        h = mix64(sh[pj] + R(g, v) + (unsigned long long)(tt + 1) * kGamma);
+      }
+      // usually every active lane of a round closes cycles of one slot (one warp sum,
+      // one atomic); otherwise per lane
+      const unsigned int g0 = __shfl_sync(0xffffffffu, g, 0);  // lane 0 is active (n > r0)
+      if (__all_sync(0xffffffffu, g == g0 || i >= n)) {
+        const unsigned long long sum = warp_sum_u64(h);
+        if (lane == 0) atomicAdd(&p.hash[g0], sum);
+      } else if (i < n) {
+        atomicAdd(&p.hash[g], h);
+      }
+    }
+    __syncwarp();
+  };
+  unsigned long long m[P];
+  auto list_and_work = [&](bool children) {
+    unsigned int cnt = 0;
+#pragma unroll
+    for (int j = 0; j < P; ++j) cnt += __popcll(m[j]);
+    unsigned int incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned int y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= (unsigned)o) incl += y;
+    }
+    const unsigned int excl = incl - cnt, total = __shfl_sync(0xffffffffu, incl, 31);
+    // a child list's slots: one atomic, issued before the listing so that its round trip
+    // overlaps it
+    unsigned long long base = 0;
+    if (children && total && lane == 0) base = atomicAdd(&p.ctl->cnt[s % 3], (unsigned long long)total);
+    for (unsigned int c0 = 0; c0 < total; c0 += CL) {
+      if (cnt && excl < c0 + CL && excl + cnt > c0) {
+        unsigned int idx = excl;
+#pragma unroll
+        for (int j = 0; j < P; ++j) {
+          unsigned long long b = m[j];
+          while (b) {
+            const unsigned int v = __ffsll((long long)b) - 1;
+            b &= b - 1;
+            if (idx >= c0 && idx < c0 + CL) sl[idx - c0] = (unsigned int)(j * 32 + lane) << 8 | v;
+            ++idx;
+          }
+        }
+      }
+      if (children) flush_children(min(CL, total - c0), base + c0);
+      else flush_closings(min(CL, total - c0));
+    }
   };
 
   const unsigned int pf = p.pf >= 1 && p.pf <= (unsigned)P ? p.pf : (unsigned)P;
@@ -1136,40 +1109,10 @@ __device__ __forceinline__ void process_multi_flat(const EngineParams& p, const 
     if (c0 >= total) break;
     const unsigned long long cend = pl.begin + min(c0 + chunk, total);
     for (unsigned long long wb = pl.begin + c0; wb < cend; wb += RW) {
-      const unsigned long long t0 = wb + lane;
-      unsigned long long N[P], C[P], H[P];
-      unsigned int M[P];
-#pragma unroll
-      for (int j = 0; j < P; ++j) {
-        const unsigned long long i = t0 + (unsigned long long)j * 32ull;
-        C[j] = ((unsigned)j < pf && i < cend) ? ldcg64(sC + i) : 0ull;
-        const bool valid = C[j] != 0ull;  // (C = 0: an empty slot)
-        N[j] = valid ? ldcg64(sN + i) : 0ull;
-        H[j] = valid ? ldcg64(sH + i) : 0ull;
-        M[j] = valid ? ldcg32(sM + i) : 0xFFFFFFFFu;
-      }
-      // the round's children and their slots (one atomic, in flight during the listing)
-      unsigned int cnt = 0;
-#pragma unroll
-      for (int j = 0; j < P; ++j) cnt += __popcll(C[j]);
-      unsigned int incl = cnt;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const unsigned int y = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= (unsigned)o) incl += y;
-      }
-      const unsigned int excl = incl - cnt, ctot = __shfl_sync(0xffffffffu, incl, 31);
-      if (ctot == 0) continue;  // a round of empty slots only
-      unsigned long long base = 0;
-      if (lane == 0) base = atomicAdd(&p.ctl->cnt[s % 3], (unsigned long long)ctot);
-      // the graph of the round's first record (there is one: ctot > 0): stage it if it changed
-      unsigned int g0 = 0xFFFFFFFFu;
-#pragma unroll
-      for (int j = 0; j < P; ++j) {
-        const unsigned int bal = __ballot_sync(0xffffffffu, M[j] != 0xFFFFFFFFu);
-        if (g0 == 0xFFFFFFFFu && bal) g0 = __shfl_sync(0xffffffffu, M[j], __ffs(bal) - 1) >> 18;
-      }
+      // the graph of the round's first record (always valid): stage it if it changed
+      const unsigned int g0 = ldcg32(sM + wb) >> 18;
       if (g0 != cg) {
+        __syncwarp();
         ga[lane] = __ldg(adj + (unsigned long long)g0 * 64ull + lane);
         ga[lane + 32] = __ldg(adj + (unsigned long long)g0 * 64ull + lane + 32);
         gr[lane] = __ldg(rtab + (unsigned long long)g0 * 64ull + lane);
@@ -1178,45 +1121,66 @@ __device__ __forceinline__ void process_multi_flat(const EngineParams& p, const 
         cg = g0;
         __syncwarp();
       }
+      const unsigned long long t0 = wb + lane;
+      unsigned long long ch[P];
+      unsigned int key[P], nc[P], nk[P];
 #pragma unroll
       for (int j = 0; j < P; ++j) {
-        const bool valid = M[j] != 0xFFFFFFFFu;
-        const unsigned int v1 = M[j] & 63u, tt = (M[j] >> 12) & 63u, g = M[j] >> 18;
+        const unsigned long long i = t0 + (unsigned long long)j * 32ull;
+        const bool valid = (unsigned)j < pf && i < cend;
+        const unsigned long long B = valid ? ldcg64(sB + i) : ~0ull;
+        const unsigned long long H = valid ? ldcg64(sH + i) : 0ull;
+        const unsigned int M = valid ? ldcg32(sM + i) : 0u;
+        const unsigned int v1 = M & 63u, vt = (M >> 6) & 63u, tt = (M >> 12) & 63u, g = M >> 18;
         const unsigned int Lr = valid ? (g == cg ? cL : p.Lg[g]) : 0u;
+        const unsigned long long at = A(g, vt), a1 = A(g, v1);
+        const unsigned long long cand = at & ~B;
+        m[j] = (tt + 1 <= Lr) ? (cand & a1) : 0ull;
+        ch[j] = (store && tt + 1 < Lr) ? (cand & ~a1) : 0ull;
         const unsigned int pj = j * 32 + lane;
-        snb[pj] = N[j];
-        sh[pj] = H[j];
-        smeta[pj] = v1 | (tt << 6) | (g << 12) | ((tt + 2 <= Lr) ? 0x40000000u : 0u) |
-                    ((tt + 2 < Lr) ? 0x80000000u : 0u);
-        account(prun, p, s, valid ? (g << 6 | tt) : 0xFFFFFFFFu, valid ? 1u : 0u, __popcll(C[j]), 0u, 0u, 0ull);
+        snb[pj] = B | at;
+        sh[pj] = H;
+        smeta[pj] = v1 | (tt << 6) | (g << 12) | ((tt + 2 < Lr) ? 0x80000000u : 0u);
+        key[j] = valid ? (g << 6 | tt) : 0xFFFFFFFFu;
+        nc[j] = __popcll(m[j]);
+        nk[j] = __popcll(ch[j]);
       }
-      // list the children (path, w) and work them off CL at a time
-      base = __shfl_sync(0xffffffffu, base, 0);
-      unsigned long long next = base;
-      for (unsigned int l0 = 0; l0 < ctot; l0 += CL) {
-        if (cnt && excl < l0 + CL && excl + cnt > l0) {
-          unsigned int idx = excl;
+      // per (slot, length) counts, as runs of one key (no hash here: closings add theirs)
 #pragma unroll
-          for (int j = 0; j < P; ++j) {
-            unsigned long long b = C[j];
-            while (b) {
-              const unsigned int w = __ffsll((long long)b) - 1;
-              b &= b - 1;
-              if (idx >= l0 && idx < l0 + CL) sl[idx - l0] = (unsigned int)(j * 32 + lane) << 8 | w;
-              ++idx;
-            }
+      for (int j = 0; j < P; ++j) {
+        const unsigned int k = key[j];
+        const bool v = k != 0xFFFFFFFFu;
+        const bool m0 = v && k == run.key;
+        if (m0) run.add(nc[j], nk[j], 0ull);
+        const unsigned int rest = __ballot_sync(0xffffffffu, v && !m0);
+        if (rest) {
+          run.flush(p, s);
+          run.key = __shfl_sync(0xffffffffu, k, 31 - __clz(rest));
+          const bool m1 = v && !m0 && k == run.key;
+          if (m1) run.add(nc[j], nk[j], 0ull);
+          unsigned int pending = __ballot_sync(0xffffffffu, v && !m0 && !m1);
+          while (pending) {
+            const int leader = __ffs(pending) - 1;
+            const unsigned int lk = __shfl_sync(0xffffffffu, k, leader);
+            const bool mine = k == lk;
+            const unsigned int grp = __ballot_sync(0xffffffffu, mine);
+            StatRun one;
+            one.key = lk;
+            if (mine) one.add(nc[j], nk[j], 0ull);
+            one.flush(p, s);
+            pending &= ~grp;
           }
         }
-        next += flush_children(min(CL, ctot - l0), next);
       }
-      // the range's remaining slots (children without children): empty
-      for (unsigned long long q = next + lane; q < base + ctot; q += 32) {
-        if (q < ds) dC[q] = 0ull;
+      list_and_work(false);
+      if (store) {
+#pragma unroll
+        for (int j = 0; j < P; ++j) m[j] = ch[j];
+        list_and_work(true);
       }
     }
   }
-  prun.flush(p, s);
-  crun.flush(p, s);
+  run.flush(p, s);
   const unsigned long long tot = warp_sum_u64(nx);
   if (lane == 0 && tot) atomicAdd(&p.ctl->nxt[s % 3], tot);
 }

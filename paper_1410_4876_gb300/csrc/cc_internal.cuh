@@ -16,12 +16,7 @@
 //          test and the chord test of Algorithm 3 iff v is not in B.
 //       H  sum of r(original id) over the path's vertices (running cycle-hash input).
 //       M  v_1 | v_t << 16 (relabelled ids).
-//   bitset, many graphs (n <= 64, one word per row): N (u64), C (u64), H (u64), M (u32)
-//       N  blocked set of the path's children: B | Adj(v_t)
-//       C  the path's children, Adj(v_t) & ~B & ~Adj(v_1) (their last vertices; empty when
-//          the children would reach L'); a path is stored only if C is not empty, its
-//          closings having been counted when it was created
-//       H  as above;  M = v1 | t << 12 | slot << 18.
+//   bitset, many graphs (n <= 64, W = 1): same planes, M = v1 | vt<<6 | t<<12 | slot<<18.
 //   CSR, one graph: one record per path, its relabelled u16 ids in order padded with 0xFFFF
 //       to a multiple of 8 ids (16-byte vector accesses).
 #pragma once
@@ -478,10 +473,6 @@ __host__ __device__ __forceinline__ unsigned long long round_up(unsigned long lo
 // Record bytes: bitset planes (8W + 12), CSR records (2 csr_rec_u16(t)).
 __host__ __device__ __forceinline__ unsigned long long bitset_region_bytes(unsigned long long stride, int W) {
   return round_up(stride * (8ull * W + 12ull), 256);
-}
-// Batch records: N, C, H (u64 planes) and M (u32 plane), 28 bytes.
-__host__ __device__ __forceinline__ unsigned long long multi_region_bytes(unsigned long long stride) {
-  return round_up(stride * 28ull, 256);
 }
 __host__ __device__ __forceinline__ unsigned int csr_rec_u16(unsigned int t) { return (t + 7u) & ~7u; }
 __host__ __device__ __forceinline__ unsigned long long csr_region_bytes(unsigned long long stride, unsigned t) {

@@ -534,23 +534,17 @@ __global__ void __launch_bounds__(128) label_seed_multi_kernel(
   __syncwarp();
   const unsigned int L = (max_len == 0 || max_len > n) ? n : max_len;
   if (lane == 0) p.Lg[slot] = (unsigned char)L;
-  // initial triplets <x, u, y> (u < x < y in label order) and triangles.  A triplet's own
-  // candidates Adj(y) & ~B (B = Adj(u) plus every vertex whose label is <= l(u)) are
-  // settled here: those adjacent to x close cycles of 4 vertices, the rest are its
-  // children; it is stored (batch record N, C, H, M) only if it has children.
-  const bool paths_ok = L > 3, close4 = L >= 4, child_ok = L > 4;
-  unsigned long long ntri = 0, ntri4 = 0, hacc = 0, ntrip = 0;
-  unsigned int nstore = 0;
+  // initial triplets and triangles
+  unsigned long long ntri = 0, hacc = 0;
+  unsigned int npath = 0;
   for (unsigned int u = lane; u < n; u += 32) {
     const unsigned long long au = s_row[wl][u];
-    const unsigned long long B = au | ((2ull << u) - 1ull);
     unsigned long long xs = au & ~((2ull << u) - 1ull);
     while (xs) {
       const unsigned int x = __ffsll((long long)xs) - 1;
       xs &= xs - 1;
-      const unsigned long long ax = s_row[wl][x];
       const unsigned long long ys = au & ~((2ull << x) - 1ull);
-      const unsigned long long tri = ys & ax;
+      const unsigned long long tri = ys & s_row[wl][x];
       ntri += __popcll(tri);
       unsigned long long b = tri;
       while (b) {
@@ -558,29 +552,11 @@ __global__ void __launch_bounds__(128) label_seed_multi_kernel(
         b &= b - 1;
         hacc += mix64(s_r[wl][x] + s_r[wl][u] + s_r[wl][y] + 3ull * kGamma);
       }
-      if (!paths_ok) continue;
-      unsigned long long ps = ys & ~ax;
-      ntrip += __popcll(ps);
-      const unsigned long long h3 = s_r[wl][x] + s_r[wl][u];
-      while (ps) {
-        const unsigned int y = __ffsll((long long)ps) - 1;
-        ps &= ps - 1;
-        const unsigned long long cand = s_row[wl][y] & ~B;
-        if (close4) {
-          unsigned long long close = cand & ax;
-          while (close) {
-            const unsigned int z = __ffsll((long long)close) - 1;
-            close &= close - 1;
-            ++ntri4;
-            hacc += mix64(h3 + s_r[wl][y] + s_r[wl][z] + 4ull * kGamma);
-          }
-        }
-        if (child_ok && (cand & ~ax)) ++nstore;
-      }
+      if (L > 3) npath += __popcll(ys & ~s_row[wl][x]);
     }
   }
   if (L < 3) ntri = 0, hacc = 0;
-  unsigned int incl = nstore;
+  unsigned int incl = npath;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
     unsigned int y = __shfl_up_sync(0xffffffffu, incl, o);
@@ -589,12 +565,11 @@ __global__ void __launch_bounds__(128) label_seed_multi_kernel(
   const unsigned int wtot = __shfl_sync(0xffffffffu, incl, 31);
   unsigned long long base = 0;
   if (lane == 31 && wtot) base = atomicAdd(slot_counter, (unsigned long long)wtot);
-  base = __shfl_sync(0xffffffffu, base, 31) + (incl - nstore);
+  base = __shfl_sync(0xffffffffu, base, 31) + (incl - npath);
   unsigned long long nx = 0;
-  if (nstore) {
-    unsigned long long* dN = (unsigned long long*)(p.arena + frame_base);
-    unsigned long long* dC = dN + stride;
-    unsigned long long* dH = dC + stride;
+  if (npath) {
+    unsigned long long* dB = (unsigned long long*)(p.arena + frame_base);
+    unsigned long long* dH = dB + stride;
     unsigned int* dM = (unsigned int*)(dH + stride);
     unsigned long long slotpos = base;
     for (unsigned int u = lane; u < n; u += 32) {
@@ -604,39 +579,31 @@ __global__ void __launch_bounds__(128) label_seed_multi_kernel(
       while (xs) {
         const unsigned int x = __ffsll((long long)xs) - 1;
         xs &= xs - 1;
-        const unsigned long long ax = s_row[wl][x];
-        unsigned long long ps = au & ~((2ull << x) - 1ull) & ~ax;
+        unsigned long long ps = au & ~((2ull << x) - 1ull) & ~s_row[wl][x];
         while (ps) {
           const unsigned int y = __ffsll((long long)ps) - 1;
           ps &= ps - 1;
-          const unsigned long long ay = s_row[wl][y];
-          const unsigned long long ch = ay & ~B & ~ax;
-          if (!ch) continue;
           if (slotpos >= stride) { set_err(p.ctl, kDevSeedCap, 1); ps = 0; xs = 0; break; }
-          dN[slotpos] = B | ay;
-          dC[slotpos] = ch;
+          dB[slotpos] = B;
           dH[slotpos] = s_r[wl][x] + s_r[wl][u] + s_r[wl][y];
-          dM[slotpos] = x | (3u << 12) | (slot << 18);
-          nx += __popcll(ch);
+          dM[slotpos] = x | (y << 6) | (3u << 12) | (slot << 18);
+          if (L > 4) nx += __popcll(s_row[wl][y] & ~B & ~s_row[wl][x]);
           ++slotpos;
         }
       }
     }
   }
   ntri = warp_sum_u64(ntri);
-  ntri4 = warp_sum_u64(ntri4);
   hacc = warp_sum_u64(hacc);
   nx = warp_sum_u64(nx);
-  ntrip = warp_sum_u64(ntrip);
-  const unsigned long long nst = warp_sum_u64(nstore);
+  const unsigned long long np = warp_sum_u64(npath);
   if (lane == 0) {
     const unsigned long long h = (unsigned long long)slot * kMultiHistStride;
     if (ntri) atomicAdd(&p.hist[h + 3], ntri);
-    if (ntri4) atomicAdd(&p.hist[h + 4], ntri4);
     if (hacc) atomicAdd(&p.hash[slot], hacc);
-    if (ntrip) atomicAdd(&p.tcount[h + 3], ntrip);
+    if (np) atomicAdd(&p.tcount[h + 3], np);
     if (nx) atomicAdd(next_counter, nx);
-    if (p.live && nst) atomicAdd((unsigned long long*)&p.live[slot], nst);
+    if (p.live) atomicAdd((unsigned long long*)&p.live[slot], np);
   }
 }
 
