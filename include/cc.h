@@ -424,6 +424,25 @@ cc_status cc_serve_step(cc_server* srv, cc_completion* out, uint32_t cap, uint32
 uint64_t cc_serve_predict_bytes(uint32_t n, uint64_t m, uint32_t max_degree);
 
 /*
+ * Niche overlap graph of a food web (Section 5: the paper's food-web graphs are turned into
+ * undirected niche overlap graphs, after Wilson and Watkins, before their chordless cycles
+ * are enumerated).  The food web is a directed graph on n species in CSR form: prey_idx[
+ * prey_ptr[x] .. prey_ptr[x+1]) are the species x feeds on (an arc x -> z; duplicates and
+ * cannibalism x -> x are allowed).  Two distinct species are adjacent in the niche overlap
+ * graph when they have a prey in common.  The result is a simple undirected graph in CSR
+ * form with sorted rows, ready for cc_graph_load:
+ *   out_row_ptr  host array of n + 1 entries, always filled
+ *   out_col      host array of col_capacity entries
+ *   out_nnz      receives row_ptr[n] (twice the number of edges)
+ * Runs on the context's stream and device.  Errors: CC_ERR_ARG, CC_ERR_INVALID_GRAPH (offsets
+ * not monotone, a prey id >= n), CC_ERR_UNSUPPORTED (n > cc_limits.max_n_csr),
+ * CC_ERR_TRUNCATED (col_capacity < *out_nnz: call again with a larger array), CC_ERR_OOM,
+ * CC_ERR_CUDA.
+ */
+cc_status cc_niche_overlap(cc_context* ctx, uint32_t n, const uint32_t* prey_ptr, const uint32_t* prey_idx,
+                           uint32_t* out_row_ptr, uint32_t* out_col, uint64_t col_capacity, uint64_t* out_nnz);
+
+/*
  * Allocation-free enumeration (the paper has no counterpart; this is a deployment aid).
  *
  * For callers that cannot allocate memory while they run: a plugin or real-time loop whose

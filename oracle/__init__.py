@@ -5,5 +5,5 @@ import this package.  It shares no code with the CUDA path; see ``cc_oracle.c``.
 """
 from .oracle import (  # noqa: F401
     Result, build, bruteforce, cycle_hash, degree_labeling, enumerate_cycles,
-    enumerate_parallel, splitmix64_next, triplet_count, vertex_hash,
+    enumerate_parallel, niche_overlap, splitmix64_next, triplet_count, vertex_hash,
 )

@@ -13,6 +13,9 @@
  *                          T is processed as a LIFO stack (the paper leaves the order open).
  *   cco_bruteforce       - the definition itself (Section 1): every vertex subset S, |S| >= 3,
  *                          whose induced subgraph is connected with every degree equal to 2.
+ *   cco_niche_overlap    - the niche overlap graph of a food web (Section 5, after Wilson and
+ *                          Watkins): distinct species x, y are adjacent when some species z is
+ *                          a prey of both (arcs x -> z and y -> z).
  *
  * Lengths count vertices.  max_len bounds the cycle length (0 = no bound); a path of t
  * vertices is kept for expansion only while t < L' = min(max_len, n).
@@ -304,4 +307,28 @@ uint64_t cco_triplet_count(uint32_t n, const uint32_t* row_ptr, const uint32_t* 
       }
   free(label);
   return cnt;
+}
+
+/* ------------------------------------------------------------------ niche overlap graph */
+
+/* Section 5: the food webs are turned into niche overlap graphs.  prey_idx[prey_ptr[x] ..
+ * prey_ptr[x+1]) lists the prey of x (arcs x -> z).  x != y are adjacent iff they share a
+ * prey.  Writes the CSR with ascending rows; out_col needs room for n (n - 1) ids.
+ * Returns row_ptr[n]. */
+uint64_t cco_niche_overlap(uint32_t n, const uint32_t* prey_ptr, const uint32_t* prey_idx, uint32_t* out_row_ptr,
+                           uint32_t* out_col) {
+  uint64_t nnz = 0;
+  for (uint32_t x = 0; x < n; ++x) {
+    out_row_ptr[x] = (uint32_t)nnz;
+    for (uint32_t y = 0; y < n; ++y) {
+      if (y == x) continue;
+      int share = 0;
+      for (uint32_t a = prey_ptr[x]; a < prey_ptr[x + 1] && !share; ++a)
+        for (uint32_t b = prey_ptr[y]; b < prey_ptr[y + 1]; ++b)
+          if (prey_idx[a] == prey_idx[b]) { share = 1; break; }
+      if (share) out_col[nnz++] = y;
+    }
+  }
+  out_row_ptr[n] = (uint32_t)nnz;
+  return nnz;
 }

@@ -54,6 +54,8 @@ def _load():
             lib.cco_bruteforce.restype = ctypes.c_int
             lib.cco_bruteforce.argtypes = [ctypes.c_uint32, _u32p, _u32p, ctypes.c_uint32, _u64p, _u64p,
                                            _u32p, _u64p, ctypes.c_uint64, ctypes.c_uint64, _u64p, _u64p]
+            lib.cco_niche_overlap.restype = ctypes.c_uint64
+            lib.cco_niche_overlap.argtypes = [ctypes.c_uint32, _u32p, _u32p, _u32p, _u32p]
             lib.cco_triplet_count.restype = ctypes.c_uint64
             lib.cco_triplet_count.argtypes = [ctypes.c_uint32, _u32p, _u32p]
             _lib = lib
@@ -189,3 +191,13 @@ def enumerate_parallel(g, max_len: int = 0, threads: int = 0) -> Result:
     hist = sum(p.hist for p in parts)
     tcount = sum(p.tcount for p in parts)
     return Result(hist, sum(p.hash for p in parts) % (1 << 64), tcount, None)
+
+
+def niche_overlap(n: int, prey_ptr, prey_idx):
+    """Niche overlap graph of a food web by its definition (Section 5): (row_ptr, col)."""
+    rp = np.ascontiguousarray(prey_ptr, dtype=np.uint32)
+    pi = np.ascontiguousarray(prey_idx if len(prey_idx) else [0], dtype=np.uint32)
+    out_rp = np.zeros(n + 1, dtype=np.uint32)
+    out_col = np.zeros(max(n * (n - 1), 1), dtype=np.uint32)
+    nnz = int(_load().cco_niche_overlap(n, _p32(rp), _p32(pi), _p32(out_rp), _p32(out_col)))
+    return out_rp, out_col[:nnz].copy()

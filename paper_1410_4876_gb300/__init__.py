@@ -5,4 +5,4 @@
 seeded synthetic graph generators.  Submodules are imported on demand so that the
 generators can be used without the CUDA library.
 """
-__all__ = ["cc", "inputs", "build", "serve"]
+__all__ = ["cc", "inputs", "build"]

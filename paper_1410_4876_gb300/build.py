@@ -16,7 +16,7 @@ ROOT = os.path.dirname(HERE)
 SRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libcc.so")
-UNITS = ["cc_seed.cu", "cc_engine.cu", "cc_api.cu", "cc_serve.cu", "cc_noalloc.cu", "cc_tune.cu"]
+UNITS = ["cc_seed.cu", "cc_engine.cu", "cc_api.cu", "cc_serve.cu", "cc_noalloc.cu", "cc_tune.cu", "cc_niche.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -150,6 +150,8 @@ SIGNATURES = {
     "cc_tune": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_uint32, ctypes.c_char_p, ctypes.POINTER(cc_tune_result)]),
     "cc_tune_batch": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_uint32, _u32p, _u64p, _u32p, _u64p, _u32p,
                                        ctypes.c_uint32, ctypes.c_char_p, ctypes.POINTER(cc_tune_result)]),
+    "cc_niche_overlap": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_uint32, _u32p, _u32p, _u32p, _u32p,
+                                          ctypes.c_uint64, _u64p]),
     "cc_enumerate_noalloc": (ctypes.c_int32, [ctypes.c_uint32, _u32p, _u32p, ctypes.c_uint32, ctypes.c_void_p,
                                               _u64p, _u64p, _u64p]),
 }
@@ -327,6 +329,23 @@ def cc_batch_submit(ctx, graphs: Sequence, max_len: int = 0):
     s = load_library().cc_batch_submit(ctx, len(graphs), _p32(ns), _p64(row_off), _p32(rp), _p64(col_off), _p32(cl),
                                        max_len, ctypes.byref(bid))
     return s, int(bid.value)
+
+
+def cc_niche_overlap(ctx, n: int, prey_ptr, prey_idx, col_capacity: Optional[int] = None):
+    """Niche overlap graph of a food web: (status, row_ptr, col).  With col_capacity None
+    the call is made twice (sizes, then ids)."""
+    pp = np.ascontiguousarray(prey_ptr, dtype=np.uint32)
+    pi = np.ascontiguousarray(prey_idx if len(prey_idx) else np.zeros(1), dtype=np.uint32)
+    rp = np.zeros(n + 1, dtype=np.uint32)
+    nnz = ctypes.c_uint64(0)
+    cap = 0 if col_capacity is None else col_capacity
+    col = np.zeros(max(cap, 1), dtype=np.uint32)
+    s = load_library().cc_niche_overlap(ctx, n, _p32(pp), _p32(pi), _p32(rp), _p32(col), cap, ctypes.byref(nnz))
+    if s == CC_ERR_TRUNCATED and col_capacity is None:
+        cap = int(nnz.value)
+        col = np.zeros(max(cap, 1), dtype=np.uint32)
+        s = load_library().cc_niche_overlap(ctx, n, _p32(pp), _p32(pi), _p32(rp), _p32(col), cap, ctypes.byref(nnz))
+    return s, rp, col[:int(nnz.value)]
 
 
 def cc_batch_load(ctx, packed):

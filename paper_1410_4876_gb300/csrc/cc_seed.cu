@@ -1,10 +1,11 @@
 // Degree labelling (Section 2) and initial triplets / triangles (Section 4.3, Algorithm 2).
 //
-// The labelling is inherently sequential (Section 4 keeps it on the host); here one warp
+// The labelling is inherently sequential (Section 4 keeps it on the host; Section 6 proposes
+// degree updates by one processor per edge and a parallel minimum per step); here one warp
 // runs it on the device so the whole enumeration stays on the GPU with no host round
 // trip.  Each step takes the live vertex of minimum current degree (ties: smallest id),
-// which is found from per-32-vertex group minima with one warp reduction, then lowers
-// its neighbours' degrees.  Vertices are then renumbered by label (new id = label - 1),
+// found by one warp reduction over a two-level tree of minima (32-vertex groups, 32-group
+// supergroups), while the lanes lower its neighbours' degrees in parallel.  Vertices are then renumbered by label (new id = label - 1),
 // so "l(x) < l(y)" becomes "x < y" and every label test is an integer or bit-mask test.
 //
 // Seeding replaces the |V| * Delta^2 flat thread grid of Algorithm 2 (most of whose
@@ -18,8 +19,19 @@ namespace cc {
 
 // ------------------------------------------------------------------ labelling, one graph
 
-// Dynamic shared memory: key[n] (u32) followed by gmin[ceil(n/32)] (u32).
-// key(v) = current_degree << 16 | v for a live vertex, 0xFFFFFFFF once removed.
+// Dynamic shared memory: key[n] (u32), gmin[G] (u32), sgmin[32] (u32), G = ceil(n / 32).
+// key(v) = current_degree << 16 | v for a live vertex, 0xFFFFFFFF once removed.  gmin[g]
+// is the smallest key of the 32 vertices of group g, sgmin[s] the smallest of the 32 group
+// minima of supergroup s (n <= 32768 gives at most 32 supergroups, one per lane).
+//
+// Each step of the labelling (Section 2: remove a vertex of minimum current degree, ties
+// by smallest id) is one warp reduction over sgmin.  Removing u lowers its neighbours'
+// keys, and only keys of u's own group and supergroup can rise (u's key becomes dead), so
+// a step recomputes gmin of u's group (one load per lane: the group's keys, with the
+// neighbours' new keys folded in) and sgmin of u's supergroup (one load per lane), and
+// lowers every other affected minimum by atomicMin.  The row of u, its neighbours' keys
+// and the group's keys are loaded side by side, so a step is a short chain of dependent
+// shared-memory accesses and two reductions.
 __global__ void __launch_bounds__(1024) label_single_kernel(const unsigned int* __restrict__ row_ptr,
                                                             const unsigned int* __restrict__ col, unsigned int n,
                                                             int W, unsigned int* perm, unsigned int* newid,
@@ -30,11 +42,12 @@ __global__ void __launch_bounds__(1024) label_single_kernel(const unsigned int* 
   unsigned int* key = sm_label;
   const unsigned int G = (n + 31) / 32;
   unsigned int* gmin = sm_label + n;
+  unsigned int* sgmin = gmin + G;
   const unsigned int tid = threadIdx.x, lane = tid & 31;
   const unsigned int kDead = 0xFFFFFFFFu;
   if (stage_csr) {
     // the sequential loop below reads a row per step: keep the CSR in shared memory
-    unsigned int* rp_s = gmin + G;
+    unsigned int* rp_s = sgmin + 32;
     unsigned int* col_s = rp_s + n + 1;
     const unsigned int nnz = row_ptr[n];
     for (unsigned int i = tid; i <= n; i += blockDim.x) rp_s[i] = row_ptr[i];
@@ -43,44 +56,58 @@ __global__ void __launch_bounds__(1024) label_single_kernel(const unsigned int* 
     row_ptr = rp_s;
     col = col_s;
   }
-
+  for (unsigned int v = tid; v < n; v += blockDim.x) key[v] = ((row_ptr[v + 1] - row_ptr[v]) << 16) | v;
+  __syncthreads();
+  for (unsigned int g = tid; g < G; g += blockDim.x) {
+    unsigned int m = kDead;
+    for (unsigned int j = 0; j < 32; ++j) {
+      const unsigned int v = g * 32 + j;
+      if (v < n) m = min(m, key[v]);
+    }
+    gmin[g] = m;
+  }
+  __syncthreads();
   if (tid < 32) {
-    for (unsigned int v = lane; v < n; v += 32) key[v] = ((row_ptr[v + 1] - row_ptr[v]) << 16) | v;
-    __syncwarp();
-    for (unsigned int g = lane; g < G; g += 32) {
+    {
       unsigned int m = kDead;
-      for (unsigned int j = 0; j < 32; ++j) {
-        unsigned int v = g * 32 + j;
-        if (v < n) m = min(m, key[v]);
-      }
-      gmin[g] = m;
+      for (unsigned int g = lane * 32; g < G && g < lane * 32 + 32; ++g) m = min(m, gmin[g]);
+      sgmin[lane] = m;  // (lanes past the last supergroup hold dead)
     }
     __syncwarp();
     for (unsigned int i = 0; i < n; ++i) {
-      unsigned int m = kDead;
-      for (unsigned int g = lane; g < G; g += 32) m = min(m, gmin[g]);
-      m = __reduce_min_sync(0xffffffffu, m);
-      const unsigned int u = m & 0xFFFFu;
-      if (lane == 0) {
-        perm[i] = u;
-        newid[u] = i;
-        key[u] = kDead;
-      }
-      __syncwarp();
-      const unsigned int gu = u >> 5, v = gu * 32 + lane;
-      unsigned int k = v < n ? key[v] : kDead;
-      k = __reduce_min_sync(0xffffffffu, k);
-      if (lane == 0) gmin[gu] = k;
-      __syncwarp();
-      for (unsigned int e = row_ptr[u] + lane; e < row_ptr[u + 1]; e += 32) {
+      const unsigned int m = __reduce_min_sync(0xffffffffu, sgmin[lane]);
+      const unsigned int u = m & 0xFFFFu, gu = u >> 5, su = gu >> 5;
+      // u's group without u, and u's row (loaded side by side)
+      const unsigned int v = gu * 32 + lane;
+      unsigned int kg = (v < n && v != u) ? key[v] : kDead;
+      const unsigned int rb = row_ptr[u], re = row_ptr[u + 1];
+      for (unsigned int e = rb + lane; e < re; e += 32) {
         const unsigned int w = col[e];
         unsigned int kw = key[w];
         if (kw != kDead) {
           kw -= 1u << 16;
           key[w] = kw;
-          atomicMin(&gmin[w >> 5], kw);
+          const unsigned int gw = w >> 5;
+          if (gw == gu) {
+            kg = min(kg, kw);
+          } else {
+            atomicMin(&gmin[gw], kw);
+            if ((gw >> 5) != su) atomicMin(&sgmin[gw >> 5], kw);
+          }
         }
       }
+      kg = __reduce_min_sync(0xffffffffu, kg);
+      if (lane == 0) {
+        gmin[gu] = kg;
+        key[u] = kDead;
+        perm[i] = u;
+        newid[u] = i;
+      }
+      __syncwarp();
+      // u's supergroup: its groups' minima after this step's updates
+      const unsigned int g2 = su * 32 + lane;
+      const unsigned int ks = __reduce_min_sync(0xffffffffu, g2 < G ? gmin[g2] : kDead);
+      if (lane == 0) sgmin[su] = ks;
       __syncwarp();
     }
   }
@@ -215,7 +242,7 @@ cudaError_t launch_label_single(const unsigned int* row_ptr, const unsigned int*
     return cudaGetLastError();
   }
   // perm holds 2n words: perm[0..n) new->original, perm[n..2n) original->new
-  size_t smem = sizeof(unsigned int) * (n + (n + 31) / 32);
+  size_t smem = sizeof(unsigned int) * (n + (n + 31) / 32 + 32);
   const size_t csr_words = (size_t)n + 1 + nnz;
   const int stage = (smem + 4 * csr_words) <= 96 * 1024 ? 1 : 0;
   if (stage) smem += 4 * csr_words;

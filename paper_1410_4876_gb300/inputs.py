@@ -310,6 +310,42 @@ def serving_request(index: int, seed: int) -> Tuple[str, tuple]:
     return mixture_spec(index, seed + 1)
 
 
+# ---------------------------------------------------------------- food webs
+
+def niche_model_web(n: int, connectance: float, seed: int):
+    """A seeded food web of the niche model (Williams and Martinez, Nature 2000), the
+    usual synthetic stand-in for measured food webs like those of the paper's first group.
+    Returns (prey_ptr, prey_idx): species x feeds on prey_idx[prey_ptr[x] .. prey_ptr[x+1])
+    (ascending; cannibalism allowed).
+
+    Stream ``seed_key(seed)`` draws 3 uniforms per species i (draws 3i, 3i+1, 3i+2): niche
+    value v_i = u0; feeding range r_i = v_i * (1 - (1 - u1) ** (1 / beta)) with
+    beta = 1 / (2 C) - 1 (a Beta(1, beta) draw by its inverse CDF); range centre
+    c_i = r_i / 2 + u2 * (v_i - r_i / 2).  Species i eats every j with
+    c_i - r_i / 2 <= v_j <= c_i + r_i / 2.  The species with the smallest niche value gets
+    r = 0 (a basal species), as in the model."""
+    u = uniform(seed_key(seed), 3 * n).reshape(n, 3)
+    beta = 1.0 / (2.0 * connectance) - 1.0
+    v = u[:, 0]
+    r = v * (1.0 - (1.0 - u[:, 1]) ** (1.0 / beta))
+    r[np.argmin(v)] = 0.0
+    c = r / 2.0 + u[:, 2] * (v - r / 2.0)
+    lo, hi = c - r / 2.0, c + r / 2.0
+    rows = []
+    for i in range(n):
+        prey = np.nonzero((v >= lo[i]) & (v <= hi[i]) & (r[i] > 0))[0]
+        rows.append(prey.astype(np.uint32))
+    prey_ptr = np.zeros(n + 1, dtype=np.uint32)
+    prey_ptr[1:] = np.cumsum([x.size for x in rows])
+    prey_idx = np.concatenate(rows).astype(np.uint32) if n else np.zeros(0, np.uint32)
+    return prey_ptr, prey_idx
+
+
+def graph_from_csr(n: int, row_ptr, col, name: str = "") -> Graph:
+    """A Graph from a simple undirected CSR (sorted rows), e.g. a niche overlap graph."""
+    return Graph(n, np.asarray(row_ptr, dtype=np.uint32), np.asarray(col, dtype=np.uint32), name)
+
+
 # ---------------------------------------------------------------- packing helpers
 
 def pack(graphs: Sequence[Graph]):

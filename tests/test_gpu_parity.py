@@ -67,9 +67,29 @@ def test_table1_graphs(ctx, g):
     _same(ctx.enumerate(g), oracle.enumerate_cycles(g))
 
 
+def _table1_grids():
+    # k l total hash hist[4..]: totals from Table 1, histogram and hash from the oracle
+    # (tests/golden/make_table1_hashes.py)
+    import os
+    out = {}
+    for line in open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "table1_grids.txt")):
+        if line.startswith("#") or not line.strip():
+            continue
+        f = line.split()
+        out[(int(f[0]), int(f[1]))] = (int(f[2]), int(f[3], 16), [0, 0, 0, 0] + [int(x) for x in f[4:]])
+    return out
+
+
+def _same_as_table1(r, k, l):
+    total, hsh, hist = _table1_grids()[(k, l)]
+    got = [int(x) for x in r.hist]
+    while got and got[-1] == 0:
+        got.pop()
+    assert r.total == total and got == hist and r.hash == hsh
+
+
 def test_grid6x10_table1(ctx):
-    r = ctx.enumerate(I.grid(6, 10))
-    assert r.total == 800139  # Table 1
+    _same_as_table1(ctx.enumerate(I.grid(6, 10)), 6, 10)
 
 
 def test_wheel_with_hub_closed_form(ctx):
@@ -87,6 +107,7 @@ def test_large_grids_table1(ctx, k, l, total):
     r = ctx.enumerate(I.grid(k, l))
     assert r.total == total
     assert int(r.hist[3]) == 0 and int(r.hist[4]) == (k - 1) * (l - 1)
+    _same_as_table1(r, k, l)
 
 
 @pytest.mark.parametrize("max_len", [1, 2, 3, 4, 5, 8, 13])
@@ -495,3 +516,31 @@ def test_enumerate_part_arguments(cc, ctx):
         assert s == cc.CC_ERR_ARG
         r = lg.enumerate(0, part=0, nparts=1)
         assert r.total == oracle.enumerate_cycles(I.grid(4, 4)).total
+
+
+# ------------------------------------------------------------------ niche overlap graphs (Section 5)
+
+@pytest.mark.parametrize("n,C,seed", [(24, 0.15, 1), (39, 0.12, 2), (69, 0.25, 3), (128, 0.2, 4), (500, 0.05, 5),
+                                      (2000, 0.01, 6)])
+def test_niche_overlap_equals_oracle(cc, ctx, n, C, seed):
+    pp, pi = I.niche_model_web(n, C, seed)
+    s, rp, col = cc.cc_niche_overlap(ctx.handle, n, pp, pi)
+    assert s == cc.CC_OK
+    ref_rp, ref_col = oracle.niche_overlap(n, pp, pi)
+    assert rp.tolist() == ref_rp.tolist() and col.tolist() == ref_col.tolist()
+    if n <= 128:
+        # and its chordless cycles, as the paper enumerates them
+        g = I.graph_from_csr(n, rp, col)
+        _same(ctx.enumerate(g), oracle.enumerate_cycles(g))
+
+
+def test_niche_overlap_truncation_and_errors(cc, ctx):
+    pp, pi = I.niche_model_web(60, 0.2, 9)
+    s, rp, col = cc.cc_niche_overlap(ctx.handle, 60, pp, pi, col_capacity=3)
+    assert s == cc.CC_ERR_TRUNCATED and int(rp[-1]) > 3
+    s, rp2, col2 = cc.cc_niche_overlap(ctx.handle, 60, pp, pi)
+    assert s == cc.CC_OK and rp2.tolist() == rp.tolist()
+    bad = pi.copy()
+    bad[0] = 60
+    s, _, _ = cc.cc_niche_overlap(ctx.handle, 60, pp, bad)
+    assert s == cc.CC_ERR_INVALID_GRAPH

@@ -390,3 +390,50 @@ def test_parts_partition_the_definition(chunk):
         for p in range(3):
             got += oracle.enumerate_cycles(g, cycles=True, part=p, nparts=3).cycles
         assert sorted(got) == ref
+
+
+# ------------------------------------------------------------------ niche overlap graph (Section 5)
+
+def _web(n, prey_lists):
+    ptr = np.zeros(n + 1, dtype=np.uint32)
+    ptr[1:] = np.cumsum([len(p) for p in prey_lists])
+    idx = np.array([z for p in prey_lists for z in p], dtype=np.uint32)
+    return ptr, idx
+
+
+def _edges(rp, col):
+    return {(x, int(y)) for x in range(len(rp) - 1) for y in col[rp[x]:rp[x + 1]]}
+
+
+def test_niche_overlap_shared_prey_gives_a_clique():
+    # one prey (0) eaten by species 1..k: the k predators overlap pairwise (K_k); the prey
+    # itself overlaps with nobody
+    k = 6
+    rp, col = oracle.niche_overlap(k + 1, *_web(k + 1, [[]] + [[0]] * k))
+    assert _edges(rp, col) == {(x, y) for x in range(1, k + 1) for y in range(1, k + 1) if x != y}
+
+
+def test_niche_overlap_food_chain_is_empty():
+    # a food chain (species i eats i + 1): every prey has a single predator
+    n = 9
+    rp, col = oracle.niche_overlap(n, *_web(n, [[i + 1] for i in range(n - 1)] + [[]]))
+    assert rp.tolist() == [0] * (n + 1) and col.size == 0
+
+
+def test_niche_overlap_worked_example():
+    # worked by hand: 0 eats 3, 4; 1 eats 4; 2 eats 5; 3 eats itself and 5; 4, 5 basal;
+    # 6 eats 3.  Prey 3 has predators 0, 3, 6 (overlaps 0-3, 0-6, 3-6), prey 4 has 0, 1
+    # (0-1), prey 5 has 2, 3 (2-3)
+    rp, col = oracle.niche_overlap(7, *_web(7, [[3, 4], [4], [5], [3, 5], [], [], [3]]))
+    und = {(0, 1), (0, 3), (0, 6), (3, 6), (2, 3)}
+    assert _edges(rp, col) == und | {(b, a) for a, b in und}
+    assert all((np.diff(col[rp[x]:rp[x + 1]].astype(np.int64)) > 0).all() for x in range(7))
+
+
+def test_niche_model_overlap_graphs_are_simple_and_symmetric():
+    for n, C, seed in [(24, 0.15, 1), (69, 0.25, 2), (128, 0.2, 3)]:
+        rp, col = oracle.niche_overlap(n, *I.niche_model_web(n, C, seed))
+        e = _edges(rp, col)
+        assert all((y, x) in e and x != y for x, y in e)
+        g = I.graph_from_csr(n, rp, col)
+        assert g.m == len(e) // 2
