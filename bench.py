@@ -779,7 +779,7 @@ def main():
     ap.add_argument("--no-graph", action="store_true",
                     help="launch every kernel directly (no CUDA-graph replay of repeated enumerations)")
     ap.add_argument("--batch-count", type=int, default=4096)
-    ap.add_argument("--cpu-stride", type=int, default=128, help="batch: the oracle is timed on every n-th graph")
+    ap.add_argument("--cpu-stride", type=int, default=16, help="batch: the oracle is timed on every n-th graph")
     ap.add_argument("--rate", type=float, default=2000.0, help="serving: mean arrivals per second")
     ap.add_argument("--serve-seconds", type=float, default=60.0, help="serving: arrival window (s)")
     ap.add_argument("--serve-steps", type=int, default=8, help="serving: expansion steps per round")
