@@ -92,6 +92,13 @@ typedef struct cc_options {
                                /* size * 1024 for graphs of maximum degree <= 5, and no   */
                                /* cluster phase for denser ones; a nonzero value runs     */
                                /* the phase for every bitset graph                        */
+  uint32_t reserved;           /* must be 0                                               */
+  uint64_t host_frontier_bytes;/* pinned host memory for frontier frames (0 = none).  When */
+                               /* cc_enumerate would expand a level in small depth-first  */
+                               /* chunks while other frames wait below it, those frames  */
+                               /* move to host memory and come back when the device stack */
+                               /* empties (Section 6's host-GPU transport); fixed at       */
+                               /* creation.  Not used by cc_enumerate_stream or batches.  */
 } cc_options;
 
 /* cc_options.flags */
@@ -128,7 +135,7 @@ typedef struct cc_run_info {
   int32_t dev_error;       /* device-side error word (0 = none; diagnostics)          */
   int32_t dev_error_info;  /* where it was raised                                     */
   uint32_t replayed;       /* 1 if the call replayed a captured CUDA graph            */
-  uint32_t pad;
+  uint32_t host_offloads;  /* times frames were moved to host memory (host frontier)  */
 } cc_run_info;
 
 /* Optional cycle list.  Set the capacities and pointers; the call fills count,

@@ -53,6 +53,8 @@ class cc_options(ctypes.Structure):
         ("flags", ctypes.c_uint32),
         ("paths_per_thread", ctypes.c_uint32),
         ("small_phase_paths", ctypes.c_uint32),
+        ("reserved", ctypes.c_uint32),
+        ("host_frontier_bytes", ctypes.c_uint64),
     ]
 
 
@@ -86,7 +88,7 @@ class cc_run_info(ctypes.Structure):
         ("dev_error", ctypes.c_int32),
         ("dev_error_info", ctypes.c_int32),
         ("replayed", ctypes.c_uint32),
-        ("pad", ctypes.c_uint32),
+        ("host_offloads", ctypes.c_uint32),
     ]
 
 
@@ -407,7 +409,8 @@ class Context:
 
     def __init__(self, frontier_bytes: int = 0, mode: int = CC_MODE_AUTO, threads_per_block: int = 0,
                  blocks_per_sm: int = 0, spin_limit: int = 0, use_torch: bool = False, stream: int = 0,
-                 flags: int = 0, paths_per_thread: int = 0, small_phase_paths: int = 0):
+                 flags: int = 0, paths_per_thread: int = 0, small_phase_paths: int = 0,
+                 host_frontier_bytes: int = 0):
         self._ws = None
         opts = cc_options()
         opts.frontier_bytes = frontier_bytes
@@ -419,6 +422,7 @@ class Context:
         opts.flags = flags
         opts.paths_per_thread = paths_per_thread
         opts.small_phase_paths = small_phase_paths
+        opts.host_frontier_bytes = host_frontier_bytes
         if use_torch:
             import torch
             nbytes = frontier_bytes or (1 << 30)

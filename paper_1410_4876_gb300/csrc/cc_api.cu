@@ -8,6 +8,7 @@
 // followed by one device-to-host copy of the histogram, hash, level counts and status.
 #include <algorithm>
 #include <chrono>
+#include <functional>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -24,7 +25,7 @@ using namespace cc;
 static bool options_valid(const cc_options& o) {
   if (o.threads_per_block && (o.threads_per_block < 64 || o.threads_per_block > 256 || o.threads_per_block % 32))
     return false;
-  if (o.mode > CC_MODE_CSR || o.blocks_per_sm > 4 || o.paths_per_thread > 3) return false;
+  if (o.mode > CC_MODE_CSR || o.blocks_per_sm > 4 || o.paths_per_thread > 3 || o.reserved) return false;
   return true;
 }
 
@@ -100,6 +101,7 @@ extern "C" void cc_context_destroy(cc_context* c) {
   if (c->h_res) cudaFreeHost(c->h_res);
   if (c->h_ctl) cudaFreeHost(c->h_ctl);
   if (c->h_stream) cudaFreeHost(c->h_stream);
+  if (c->h_front) cudaFreeHost(c->h_front);
   if (c->ev0) cudaEventDestroy(c->ev0);
   if (c->ev1) cudaEventDestroy(c->ev1);
   if (c->ev2) cudaEventDestroy(c->ev2);
@@ -220,6 +222,120 @@ struct StreamOut {
   uint32_t rounds;
 };
 
+constexpr unsigned int kOffloadMinChunk = 4096;
+
+// Bytes of n records of a frame of paths with t vertices, packed (stride n).
+unsigned long long packed_bytes(Kind kind, int W, unsigned int t, unsigned long long n) {
+  return is_csr(kind) ? n * 2ull * csr_rec_u16(t) : n * (8ull * W + 12ull);
+}
+
+// Copies the records [first, first + n) of a frame between its device region (plane
+// stride f.stride) and a packed host block (plane stride n).
+void copy_frame_records(unsigned char* arena, const Frame& f, Kind kind, int W, unsigned long long first,
+                        unsigned long long n, unsigned char* host, bool to_host, cudaStream_t st,
+                        const std::function<void(cudaError_t)>& ok) {
+  auto cp = [&](unsigned long long dev_off, unsigned long long host_off, unsigned long long bytes) {
+    if (to_host) ok(cudaMemcpyAsync(host + host_off, arena + dev_off, bytes, cudaMemcpyDeviceToHost, st));
+    else ok(cudaMemcpyAsync(arena + dev_off, host + host_off, bytes, cudaMemcpyHostToDevice, st));
+  };
+  if (is_csr(kind)) {
+    const unsigned long long rb = 2ull * csr_rec_u16(f.t);
+    cp(f.base + first * rb, 0, n * rb);
+    return;
+  }
+  for (int q = 0; q < W; ++q) cp(f.base + 8ull * (q * f.stride + first), 8ull * q * n, 8ull * n);  // B planes
+  cp(f.base + 8ull * (W * f.stride + first), 8ull * W * n, 8ull * n);                              // H
+  cp(f.base + 8ull * (W + 1) * f.stride + 4ull * first, 8ull * (W + 1) * n, 4ull * n);             // M
+}
+
+// The host-frontier loop of one enumeration (see cc_options.host_frontier_bytes).
+cc_status host_frontier_loop(cc_context* c, Kind kind, int W, const EngineParams& p, int grid, int block, size_t smem,
+                             cc_run_info& info, const std::function<void(cudaEvent_t)>& rec) {
+  struct HostFrame {
+    unsigned int t;
+    unsigned long long n, next, ncl, off;
+  };
+  std::vector<HostFrame> hstack;
+  unsigned long long hused = 0;
+  cudaStream_t st = c->stream;
+  cudaError_t e = cudaSuccess;
+  auto ok = [&](cudaError_t x) {
+    if (e == cudaSuccess && x != cudaSuccess) e = x;
+  };
+  if (!c->h_front) {
+    if (cudaMallocHost((void**)&c->h_front, c->opts.host_frontier_bytes) != cudaSuccess) {
+      (void)cudaGetLastError();
+      return CC_ERR_OOM;
+    }
+    c->h_front_bytes = c->opts.host_frontier_bytes;
+  }
+  std::vector<Frame> fr;
+  for (;;) {
+    Control& hc = *c->h_ctl;
+    if (hc.err) return CC_OK;  // reported by the caller from the error word
+    if (hc.want_offload) {
+      // every device frame's unexpanded records to the host stack, bottom frame first
+      fr.resize(hc.depth);
+      ok(cudaMemcpyAsync(fr.data(), c->frames, sizeof(Frame) * hc.depth, cudaMemcpyDeviceToHost, st));
+      ok(cudaStreamSynchronize(st));
+      if (e != cudaSuccess) break;
+      for (const Frame& f : fr) {
+        const unsigned long long n = f.count > f.cursor ? f.count - f.cursor : 0ull;
+        if (n == 0) continue;
+        const unsigned long long bytes = packed_bytes(kind, W, f.t, n);
+        if (hused + bytes > c->h_front_bytes) return CC_ERR_CAPACITY;
+        copy_frame_records(c->arena, f, kind, W, f.cursor, n, c->h_front + hused, true, st, ok);
+        hstack.push_back({f.t, n, f.cursor == 0 ? f.next : kNoNext, f.cursor == 0 ? f.ncl : kNoNext, hused});
+        hused += (bytes + 255) & ~255ull;
+      }
+      ok(cudaStreamSynchronize(st));
+      info.host_offloads += 1;
+      hc.depth = 0;
+    } else if (hc.depth != 0 || hstack.empty()) {
+      break;  // finished (or stopped for another reason, reported by the caller)
+    }
+    if (hstack.empty()) break;
+    // the most recent host frame back, alone, at the bottom of the arena
+    const HostFrame hf = hstack.back();
+    hstack.pop_back();
+    hused = hf.off;
+    Frame f{};
+    f.base = 0;
+    f.stride = round_up(hf.n, 8);
+    f.bytes = is_csr(kind) ? csr_region_bytes(f.stride, hf.t) : bitset_region_bytes(f.stride, W);
+    f.count = hf.n;
+    f.cursor = 0;
+    f.next = hf.next;
+    f.ncl = hf.ncl;
+    f.t = hf.t;
+    f.end = 0;
+    copy_frame_records(c->arena, f, kind, W, 0, hf.n, c->h_front + hf.off, false, st, ok);
+    hc.depth = 1;
+    hc.bot = f.bytes;
+    hc.top = c->arena_bytes;
+    hc.want_offload = 0;
+    // (the frame from pageable memory is staged before the call returns; the control block
+    // is the pinned mirror, left untouched until the sync below)
+    ok(cudaMemcpyAsync(c->frames, &f, sizeof(Frame), cudaMemcpyHostToDevice, st));
+    ok(cudaMemcpyAsync(c->ctl, &hc, sizeof(Control), cudaMemcpyHostToDevice, st));
+    EngineParams q = p;
+    q.fresh = 0;
+    ok(launch_engine(kind, q, grid, block, smem, st));
+    info.launches += 1;
+    rec(c->ev1);
+    ok(cudaMemcpyAsync(c->h_res, c->d_res, c->d_res_words * 8, cudaMemcpyDeviceToHost, st));
+    ok(cudaMemcpyAsync(c->h_ctl, c->ctl, sizeof(Control), cudaMemcpyDeviceToHost, st));
+    rec(c->ev2);
+    ok(cudaStreamSynchronize(st));
+    if (e != cudaSuccess) break;
+  }
+  if (e != cudaSuccess) {
+    (void)cudaGetLastError();
+    return cuda_status(e);
+  }
+  return CC_OK;
+}
+
 cc_status enumerate_impl(cc_graph* g, uint32_t max_len, uint64_t* out_hist, uint64_t* out_hash, uint64_t* out_tcount,
                          cc_cycles* out_cycles, StreamOut* so, cc_run_info* out_info, uint32_t part = 0,
                          uint32_t nparts = 1) {
@@ -280,6 +396,7 @@ cc_status enumerate_impl(cc_graph* g, uint32_t max_len, uint64_t* out_hist, uint
     const size_t hb = 12 * capc + 4 * capv;
     if (c->h_stream_bytes < hb) {
       if (c->h_stream) cudaFreeHost(c->h_stream);
+  if (c->h_front) cudaFreeHost(c->h_front);
       c->h_stream = nullptr;
       c->h_stream_bytes = 0;
       CC_CUDA(cudaMallocHost((void**)&c->h_stream, hb));
@@ -321,6 +438,10 @@ cc_status enumerate_impl(cc_graph* g, uint32_t max_len, uint64_t* out_hist, uint
   p.seed_entries = (unsigned int)(2 * g->m);
   p.part = part;
   p.nparts = nparts;
+  // the host frontier takes over when a level would be expanded in chunks of fewer than
+  // this many paths while frames wait below it
+  const bool host_front = c->opts.host_frontier_bytes > 0 && !so;
+  p.offload_min = host_front ? kOffloadMinChunk : 0u;
   if (!c->d_trace) {
     if ((s = dev_alloc(c, (void**)&c->d_trace, 16ull * kTraceCap))) {
       free_cyc();
@@ -426,8 +547,9 @@ cc_status enumerate_impl(cc_graph* g, uint32_t max_len, uint64_t* out_hist, uint
     ok(cudaMemcpyAsync(c->h_ctl, c->ctl, sizeof(Control), cudaMemcpyDeviceToHost, st));
     rec(c->ev2);
   };
-  // CUDA graph: the key covers everything the captured work depends on
-  const bool use_graph = !listing && !(c->opts.flags & CC_FLAG_NO_GRAPH) && !g->no_graph;
+  // CUDA graph: the key covers everything the captured work depends on (a host frontier
+  // makes the call's launches depend on the run, so it is not captured)
+  const bool use_graph = !listing && !host_front && !(c->opts.flags & CC_FLAG_NO_GRAPH) && !g->no_graph;
   unsigned long long gkey = 0;
   if (use_graph) {
     const unsigned long long parts[] = {(unsigned long long)kind, (unsigned long long)grid, (unsigned long long)block,
@@ -474,8 +596,14 @@ cc_status enumerate_impl(cc_graph* g, uint32_t max_len, uint64_t* out_hist, uint
     issue();
   }
   ok(cudaStreamSynchronize(st));
-  // streamed cycle list: drain the round's cycles to the sink, reset the list counters and
-  // resume the engine from the state it left, until no frame is left
+  // host frontier: when the engine stops for want of device memory (want_offload), every
+  // frame on the device moves to pinned host memory (only its unexpanded records, packed)
+  // and the top one comes back alone at the bottom of the arena; when the device stack
+  // empties, the next frame comes back from the host.  The engine resumes each time from
+  // the state it left (Section 6 leaves such a host-GPU transport to future work).
+  cc_status hs = CC_OK;
+  if (host_front && e == cudaSuccess) hs = host_frontier_loop(c, kind, W, p, grid, block, smem, info, rec);
+
   cc_status ss = CC_OK;
   while (so && e == cudaSuccess) {
     const Control& hc = *c->h_ctl;
@@ -531,6 +659,7 @@ cc_status enumerate_impl(cc_graph* g, uint32_t max_len, uint64_t* out_hist, uint
   const Control& h = *c->h_ctl;
   s = map_dev_err(h.err);
   if (s == CC_OK) s = ss;
+  if (s == CC_OK) s = hs;
   std::memcpy(out_hist, c->h_res, sizeof(uint64_t) * (L + 1));
   if (out_tcount) std::memcpy(out_tcount, c->h_res + (L + 1), sizeof(uint64_t) * (L + 1));
   *out_hash = c->h_res[2 * (L + 1)];

@@ -213,6 +213,13 @@ __device__ bool plan_step(const EngineParams& p, LocalState& st, StepPlan& pl) {
       const unsigned long long share = maxcap / levels;
       unsigned long long ch = share > res ? (share - res) / p.maxch : 0ull;
       if (ch == 0 && maxcap >= res + p.maxch) ch = 1;
+      // host frontier: rather than expanding this level in small chunks (or failing), stop
+      // so that the host moves the frames below to host memory and resumes with the arena
+      // free (the state written back at kernel end is this step's, unchanged)
+      if (p.offload_min && st.depth >= 2 && ch < p.offload_min) {
+        if (blockIdx.x == 0) p.ctl->want_offload = 1u;
+        return false;
+      }
       if (ch == 0) {
         set_err(p.ctl, kDevCapacity, (int)t);
         return false;

@@ -48,6 +48,8 @@ struct cc_context {
   unsigned long long last_t_start = 0;  // globaltimer at the start of the last expansion
   unsigned char* h_stream = nullptr;    // pinned drain buffer of streamed cycle lists
   size_t h_stream_bytes = 0;
+  unsigned char* h_front = nullptr;     // pinned host frontier (cc_options.host_frontier_bytes)
+  size_t h_front_bytes = 0;
   // batch state (one batch in flight per context)
   struct Batch {
     cc_batch_set* set = nullptr;  // the set being enumerated

@@ -102,6 +102,7 @@ struct Control {
   unsigned long long cyc_count;   // cycles offered to the cycle list
   unsigned long long cyc_verts;   // vertices offered to the cycle list
   unsigned long long t_start;     // globaltimer when a fresh engine launch started
+  unsigned int want_offload;      // host frontier: the engine stopped to have frames moved to host memory
 };
 
 // Engine variants.  Csr16/Csr32 keep paths of up to 16/32 vertices in registers (chosen
@@ -158,6 +159,9 @@ struct EngineParams {
                                    // more paths than the list's room allows, none when it is full
   unsigned int part, nparts;       // seeding keeps only the initial triplets (and triangles) of
                                    // this part of nparts (1 = all); see triplet_part
+  unsigned int offload_min;        // host frontier on: stop (want_offload) instead of expanding a
+                                   // level in chunks of fewer paths than this while frames lie
+                                   // below it (0 = off)
 };
 
 // Triplet sharding: the part of the initial triplet or triangle <x, u, y> (l(u) < l(x) <

@@ -544,3 +544,31 @@ def test_niche_overlap_truncation_and_errors(cc, ctx):
     bad[0] = 60
     s, _, _ = cc.cc_niche_overlap(ctx.handle, 60, pp, bad)
     assert s == cc.CC_ERR_INVALID_GRAPH
+
+
+# ------------------------------------------------------------------ host frontier (Section 6)
+
+@pytest.mark.parametrize("g,L,arena", [(I.grid(7, 7), 0, 256 << 10), (I.gnm(400, 800, 9), 11, 512 << 10),
+                                       (I.gnp(60, 0.15, 7), 0, 4 << 20)])
+def test_host_frontier_equals_oracle(cc, g, L, arena):
+    # a frontier far too small for the graph: frames move to pinned host memory and back,
+    # and the result is still the oracle's
+    ref = oracle.enumerate_cycles(g, max_len=L)
+    with cc.Context(frontier_bytes=arena, host_frontier_bytes=2 << 30) as c, c.load(g) as lg:
+        r = lg.enumerate(L)
+        _same(r, ref)
+        assert r.info.host_offloads > 0 and r.info.spilled == 1
+        assert r.info.peak_bytes <= arena
+        r2 = lg.enumerate(L)  # a second call (no CUDA graph with a host frontier)
+        _same(r2, ref)
+        assert r2.info.replayed == 0
+
+
+def test_host_frontier_too_small_reports_capacity(cc):
+    g = I.grid(7, 7)
+    with cc.Context(frontier_bytes=256 << 10, host_frontier_bytes=64 << 10) as c, c.load(g) as lg:
+        s, *_ = cc.cc_enumerate(lg.handle, g.n, 0)
+        assert s == cc.CC_ERR_CAPACITY
+        # the context stays usable
+    with cc.Context(frontier_bytes=1 << 30) as c:
+        _same(c.enumerate(g), oracle.enumerate_cycles(g))
