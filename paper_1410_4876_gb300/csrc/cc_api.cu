@@ -931,7 +931,7 @@ static cc_status batch_run(cc_batch_set* bs, uint32_t max_len, cc_batch_id* out)
   p.pf = c->opts.paths_per_thread;
   p.fuse_ok = (c->opts.flags & CC_FLAG_NO_FUSE) ? 0u : 1u;
   const unsigned long long seed_stride = round_up(bs->tb_total + 8, 8);
-  const unsigned long long seed_bytes = bitset_region_bytes(seed_stride, 1);
+  const unsigned long long seed_bytes = multi_region_bytes(seed_stride);
   if (seed_bytes > c->arena_bytes / 2) return CC_ERR_CAPACITY;
   p.seed_stride = seed_stride;
   p.seed_bytes = seed_bytes;

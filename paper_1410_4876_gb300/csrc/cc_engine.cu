@@ -93,11 +93,13 @@ struct KindTraits {
 template <Kind K>
 __device__ __forceinline__ unsigned long long region_bytes(unsigned long long stride, unsigned int t_child) {
   if constexpr (KindTraits<K>::csr) return csr_region_bytes(stride, t_child);
+  else if constexpr (KindTraits<K>::multi) return multi_region_bytes(stride);
   else return bitset_region_bytes(stride, KindTraits<K>::W);
 }
 template <Kind K>
 __device__ __forceinline__ unsigned long long record_bytes(unsigned int t_child) {
   if constexpr (KindTraits<K>::csr) return 2ull * csr_rec_u16(t_child);
+  else if constexpr (KindTraits<K>::multi) return 21ull;
   else return 8ull * KindTraits<K>::W + 12ull;
 }
 
@@ -979,14 +981,17 @@ __device__ __forceinline__ void process_bitset_fused(const EngineParams& p, cons
 // The batch form of the flattened expansion (records of many graphs in one frontier; M
 // holds v1, vt, t and the graph's slot g, whose rows and r-table sit at g * 64).  Per-path
 // statistics (paths expanded, children and closings per (slot, length)) are accumulated
-// in lane order as runs of one key, as in the per-lane form; a closing's hash is added to
-// its slot's sum by one atomic per distinct slot among the lanes of a round.
+// in lane order as runs of one key, as in the per-lane form; closing hashes are summed per
+// lane while the slot stays the same and added to its sum when it changes.
 //
 // Work distribution: a warp takes contiguous chunks of the step's records from a step
 // counter (one atomic per chunk), so its rounds mostly stay inside one graph's run of
-// records while the chunks balance the load between warps.  The rows, r-table and L' of
-// the graph a warp is working on are staged in the warp's shared memory when the graph
-// changes; records of any other graph in the same round read them from global memory.
+// records while the chunks balance the load between warps.  Each record carries its exact
+// child count (N, written with it), so the warp reserves the child slots of a whole chunk
+// with one atomic before expanding it: a single counter taking one atomic per round was
+// the hot spot of the whole grid.  The rows, r-table and L' of the graph a warp is working
+// on are staged in the warp's shared memory when the graph changes; records of any other
+// graph in the same round read them from global memory.
 template <int NT>
 __device__ __forceinline__ void process_multi_flat(const EngineParams& p, const StepPlan& pl,
                                                    const unsigned long long* adj, const unsigned long long* rtab) {
@@ -1006,14 +1011,23 @@ __device__ __forceinline__ void process_multi_flat(const EngineParams& p, const 
   const unsigned long long* sB = reinterpret_cast<const unsigned long long*>(p.arena + pl.src_base);
   const unsigned long long* sH = sB + ss;
   const unsigned int* sM = reinterpret_cast<const unsigned int*>(sH + ss);
+  const unsigned char* sN = reinterpret_cast<const unsigned char*>(sM + ss);
   unsigned long long* dB = reinterpret_cast<unsigned long long*>(p.arena + pl.dst_base);
   unsigned long long* dH = dB + ds;
   unsigned int* dM = reinterpret_cast<unsigned int*>(dH + ds);
+  unsigned char* dN = reinterpret_cast<unsigned char*>(dM + ds);
   const bool store = ds != 0;
   const unsigned long long s = pl.s;
   unsigned long long nx = 0;
   StatRun run;
   run.key = 0xFFFFFFFFu;
+  unsigned long long hacc = 0;      // closing hashes of slot hkey, per lane
+  unsigned int hkey = 0xFFFFFFFFu;
+  auto flush_hash = [&]() {
+    const unsigned long long sum = warp_sum_u64(hacc);
+    if (lane == 0 && hkey != 0xFFFFFFFFu && sum) atomicAdd(&p.hash[hkey], sum);
+    hacc = 0;
+  };
   unsigned int cg = 0xFFFFFFFFu;  // graph staged in ga / gr
   unsigned int cL = 0;            // its L'
   auto A = [&](unsigned int g, unsigned int v) -> unsigned long long {
@@ -1036,7 +1050,9 @@ __device__ __forceinline__ void process_multi_flat(const EngineParams& p, const 
         dB[slot] = nb;
         dH[slot] = sh[pj] + R(g, v);
         dM[slot] = v1 | (v << 6) | ((tt + 1) << 12) | (g << 18);
-        if (meta >> 31) nx += __popcll(A(g, v) & ~nb & ~A(g, v1));
+        const unsigned int nc = (meta >> 31) ? __popcll(A(g, v) & ~nb & ~A(g, v1)) : 0u;
+        dN[slot] = (unsigned char)nc;
+        nx += nc;
       } else {
         set_err(p.ctl, kDevBounds, 1);
       }
@@ -1055,12 +1071,15 @@ __device__ __forceinline__ void process_multi_flat(const EngineParams& p, const 
         g = (meta >> 12) & 0x7FFFFu;
         h = mix64(sh[pj] + R(g, v) + (unsigned long long)(tt + 1) * kGamma);
       }
-      // usually every active lane of a round closes cycles of one slot (one warp sum,
-      // one atomic); otherwise per lane
+      // usually every active lane of a round closes cycles of one slot: summed per lane
+      // until the slot changes; otherwise one atomic per lane
       const unsigned int g0 = __shfl_sync(0xffffffffu, g, 0);  // lane 0 is active (n > r0)
       if (__all_sync(0xffffffffu, g == g0 || i >= n)) {
-        const unsigned long long sum = warp_sum_u64(h);
-        if (lane == 0) atomicAdd(&p.hash[g0], sum);
+        if (g0 != hkey) {
+          flush_hash();
+          hkey = g0;
+        }
+        hacc += h;
       } else if (i < n) {
         atomicAdd(&p.hash[g], h);
       }
@@ -1068,6 +1087,7 @@ __device__ __forceinline__ void process_multi_flat(const EngineParams& p, const 
     __syncwarp();
   };
   unsigned long long m[P];
+  unsigned long long cnext = 0, cend_slot = 0;  // the chunk's reserved child slots (warp-uniform)
   auto list_and_work = [&](bool children) {
     unsigned int cnt = 0;
 #pragma unroll
@@ -1079,10 +1099,9 @@ __device__ __forceinline__ void process_multi_flat(const EngineParams& p, const 
       if (lane >= (unsigned)o) incl += y;
     }
     const unsigned int excl = incl - cnt, total = __shfl_sync(0xffffffffu, incl, 31);
-    // a child list's slots: one atomic, issued before the listing so that its round trip
-    // overlaps it
-    unsigned long long base = 0;
-    if (children && total && lane == 0) base = atomicAdd(&p.ctl->cnt[s % 3], (unsigned long long)total);
+    // a round's children take the next slots of the chunk's reserved range
+    const unsigned long long base = cnext;
+    if (children) cnext += total;
     for (unsigned int c0 = 0; c0 < total; c0 += CL) {
       if (cnt && excl < c0 + CL && excl + cnt > c0) {
         unsigned int idx = excl;
@@ -1115,6 +1134,16 @@ __device__ __forceinline__ void process_multi_flat(const EngineParams& p, const 
     c0 = __shfl_sync(0xffffffffu, c0, 0);
     if (c0 >= total) break;
     const unsigned long long cend = pl.begin + min(c0 + chunk, total);
+    // the chunk's children (the records' exact child counts) take one range of slots
+    if (store) {
+      unsigned int nch = 0;
+      for (unsigned long long i = pl.begin + c0 + lane; i < cend; i += 32) nch += ldcg8(sN + i);
+      nch = __reduce_add_sync(0xffffffffu, nch);
+      unsigned long long b = 0;
+      if (lane == 0 && nch) b = atomicAdd(&p.ctl->cnt[s % 3], (unsigned long long)nch);
+      cnext = __shfl_sync(0xffffffffu, b, 0);
+      cend_slot = cnext + nch;
+    }
     for (unsigned long long wb = pl.begin + c0; wb < cend; wb += RW) {
       // the graph of the round's first record (always valid): stage it if it changed
       const unsigned int g0 = ldcg32(sM + wb) >> 18;
@@ -1186,7 +1215,11 @@ __device__ __forceinline__ void process_multi_flat(const EngineParams& p, const 
         list_and_work(true);
       }
     }
+    // (the children listed equal the child counts the records carry; a mismatch would be a
+    // bug, reported instead of writing into another chunk's slots)
+    if (store && cnext != cend_slot && lane == 0) set_err(p.ctl, kDevBounds, 6);
   }
+  flush_hash();
   run.flush(p, s);
   const unsigned long long tot = warp_sum_u64(nx);
   if (lane == 0 && tot) atomicAdd(&p.ctl->nxt[s % 3], tot);

@@ -16,7 +16,8 @@
 //          test and the chord test of Algorithm 3 iff v is not in B.
 //       H  sum of r(original id) over the path's vertices (running cycle-hash input).
 //       M  v_1 | v_t << 16 (relabelled ids).
-//   bitset, many graphs (n <= 64, W = 1): same planes, M = v1 | vt<<6 | t<<12 | slot<<18.
+//   bitset, many graphs (n <= 64, W = 1): same planes, M = v1 | vt<<6 | t<<12 | slot<<18,
+//       and N (u8): the path's exact number of children (0 when they would reach L').
 //   CSR, one graph: one record per path, its relabelled u16 ids in order padded with 0xFFFF
 //       to a multiple of 8 ids (16-byte vector accesses).
 #pragma once
@@ -229,6 +230,7 @@ __device__ __forceinline__ void emit_cycle(const EngineParams& p, unsigned int k
 __device__ __forceinline__ unsigned long long ldcg64(const unsigned long long* p) { return __ldcg(p); }
 __device__ __forceinline__ unsigned int ldcg32(const unsigned int* p) { return __ldcg(p); }
 __device__ __forceinline__ unsigned short ldcg16(const unsigned short* p) { return __ldcg(p); }
+__device__ __forceinline__ unsigned int ldcg8(const unsigned char* p) { return __ldcg(p); }
 
 __device__ __forceinline__ unsigned int ld_acquire_u32(const unsigned int* p) {
   unsigned int v;
@@ -477,6 +479,10 @@ __host__ __device__ __forceinline__ unsigned long long round_up(unsigned long lo
 // Record bytes: bitset planes (8W + 12), CSR records (2 csr_rec_u16(t)).
 __host__ __device__ __forceinline__ unsigned long long bitset_region_bytes(unsigned long long stride, int W) {
   return round_up(stride * (8ull * W + 12ull), 256);
+}
+// Batch records: B, H (u64 planes), M (u32 plane) and N (u8 plane), 21 bytes.
+__host__ __device__ __forceinline__ unsigned long long multi_region_bytes(unsigned long long stride) {
+  return round_up(stride * 21ull, 256);
 }
 __host__ __device__ __forceinline__ unsigned int csr_rec_u16(unsigned int t) { return (t + 7u) & ~7u; }
 __host__ __device__ __forceinline__ unsigned long long csr_region_bytes(unsigned long long stride, unsigned t) {

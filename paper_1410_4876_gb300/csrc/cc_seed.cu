@@ -598,6 +598,7 @@ __global__ void __launch_bounds__(128) label_seed_multi_kernel(
     unsigned long long* dB = (unsigned long long*)(p.arena + frame_base);
     unsigned long long* dH = dB + stride;
     unsigned int* dM = (unsigned int*)(dH + stride);
+    unsigned char* dN = (unsigned char*)(dM + stride);
     unsigned long long slotpos = base;
     for (unsigned int u = lane; u < n; u += 32) {
       const unsigned long long au = s_row[wl][u];
@@ -614,7 +615,9 @@ __global__ void __launch_bounds__(128) label_seed_multi_kernel(
           dB[slotpos] = B;
           dH[slotpos] = s_r[wl][x] + s_r[wl][u] + s_r[wl][y];
           dM[slotpos] = x | (y << 6) | (3u << 12) | (slot << 18);
-          if (L > 4) nx += __popcll(s_row[wl][y] & ~B & ~s_row[wl][x]);
+          const unsigned int nc = (L > 4) ? __popcll(s_row[wl][y] & ~B & ~s_row[wl][x]) : 0u;
+          dN[slotpos] = (unsigned char)nc;  // the triplet's exact child count
+          nx += nc;
           ++slotpos;
         }
       }

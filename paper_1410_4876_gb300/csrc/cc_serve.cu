@@ -336,7 +336,7 @@ extern "C" cc_status cc_serve_step(cc_server* v, cc_completion* out, uint32_t ca
   // 2. admission (arrival order), into the top frame's free records or a new frame 0
   const bool empty = ctl.depth == 0;
   const unsigned long long room =
-      empty ? std::min<unsigned long long>(c->arena_bytes / 2 / 20, 1ull << 26) : top.stride - top.count;
+      empty ? std::min<unsigned long long>(c->arena_bytes / 2 / 21, 1ull << 26) : top.stride - top.count;
   std::vector<Request*> adm;
   unsigned long long seeds = 0, up_rows = 0, up_cols = 0;
   const size_t max_up_cols = (size_t)1024 * 64 * 63;
@@ -399,7 +399,7 @@ extern "C" cc_status cc_serve_step(cc_server* v, cc_completion* out, uint32_t ca
       const unsigned long long stride = round_up(seeds + v->o.reserve_paths, 8);
       Frame f{};
       f.base = 0;
-      f.bytes = bitset_region_bytes(stride, 1);
+      f.bytes = multi_region_bytes(stride);
       f.stride = stride;
       f.next = 0;
       f.ncl = kNoNext;
