@@ -549,10 +549,12 @@ def test_niche_overlap_truncation_and_errors(cc, ctx):
 # ------------------------------------------------------------------ host frontier (Section 6)
 
 @pytest.mark.parametrize("g,L,arena", [(I.grid(7, 7), 0, 256 << 10), (I.gnm(400, 800, 9), 11, 512 << 10),
-                                       (I.gnp(60, 0.15, 7), 0, 4 << 20)])
+                                       (I.gnp(60, 0.15, 7), 0, 1 << 20)])
 def test_host_frontier_equals_oracle(cc, g, L, arena):
     # a frontier far too small for the graph: frames move to pinned host memory and back,
-    # and the result is still the oracle's
+    # and the result is still the oracle's.  (How often frames move depends on the order in
+    # which a level's records were written, which the slot atomics leave free, so the test
+    # takes arenas small enough that some move in every run.)
     ref = oracle.enumerate_cycles(g, max_len=L)
     with cc.Context(frontier_bytes=arena, host_frontier_bytes=2 << 30) as c, c.load(g) as lg:
         r = lg.enumerate(L)
