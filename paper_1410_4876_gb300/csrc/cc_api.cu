@@ -226,7 +226,7 @@ constexpr unsigned int kOffloadMinChunk = 4096;
 
 // Bytes of n records of a frame of paths with t vertices, packed (stride n).
 unsigned long long packed_bytes(Kind kind, int W, unsigned int t, unsigned long long n) {
-  return is_csr(kind) ? n * 2ull * csr_rec_u16(t) : n * (8ull * W + 13ull);
+  return is_csr(kind) ? n * 2ull * csr_rec_u16(t) : n * (8ull * W + 12ull);
 }
 
 // Copies the records [first, first + n) of a frame between its device region (plane
@@ -246,7 +246,6 @@ void copy_frame_records(unsigned char* arena, const Frame& f, Kind kind, int W, 
   for (int q = 0; q < W; ++q) cp(f.base + 8ull * (q * f.stride + first), 8ull * q * n, 8ull * n);  // B planes
   cp(f.base + 8ull * (W * f.stride + first), 8ull * W * n, 8ull * n);                              // H
   cp(f.base + 8ull * (W + 1) * f.stride + 4ull * first, 8ull * (W + 1) * n, 4ull * n);             // M
-  cp(f.base + (8ull * (W + 1) + 4ull) * f.stride + first, (8ull * (W + 1) + 4ull) * n, n);         // N
 }
 
 // The host-frontier loop of one enumeration (see cc_options.host_frontier_bytes).

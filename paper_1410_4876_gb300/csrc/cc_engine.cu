@@ -100,7 +100,7 @@ template <Kind K>
 __device__ __forceinline__ unsigned long long record_bytes(unsigned int t_child) {
   if constexpr (KindTraits<K>::csr) return 2ull * csr_rec_u16(t_child);
   else if constexpr (KindTraits<K>::multi) return 21ull;
-  else return 8ull * KindTraits<K>::W + 13ull;
+  else return 8ull * KindTraits<K>::W + 12ull;
 }
 
 // ------------------------------------------------------------------ control (thread 0)
@@ -357,7 +357,6 @@ __device__ __forceinline__ void process_bitset(const EngineParams& p, const Step
   unsigned long long* dB = reinterpret_cast<unsigned long long*>(p.arena + pl.dst_base);
   unsigned long long* dH = dB + W * ds;
   unsigned int* dM = reinterpret_cast<unsigned int*>(dH + ds);
-  unsigned char* dN = reinterpret_cast<unsigned char*>(dM + ds);
   const bool store = ds != 0;
   const unsigned int t = pl.t, L = p.L;
   const unsigned long long s = pl.s;
@@ -435,13 +434,10 @@ __device__ __forceinline__ void process_bitset(const EngineParams& p, const Step
                 for (int q = 0; q < W; ++q) dB[q * ds + slot] = nb[q];
                 dH[slot] = H[j] + rtab[v];
                 dM[slot] = v1 | (v << 16);
-                unsigned int nc = 0;
                 if (next_ok) {
 #pragma unroll
-                  for (int q = 0; q < W; ++q) nc += __popcll(adj[(unsigned long long)v * W + q] & ~nb[q] & ~a1[q]);
+                  for (int q = 0; q < W; ++q) nx += __popcll(adj[(unsigned long long)v * W + q] & ~nb[q] & ~a1[q]);
                 }
-                dN[slot] = (unsigned char)nc;
-                nx += nc;
               } else {
                 set_err(p.ctl, kDevBounds, 1);
               }
@@ -482,7 +478,6 @@ __device__ __forceinline__ void process_bitset_fused_lane(const EngineParams& p,
   unsigned long long* dB = reinterpret_cast<unsigned long long*>(p.arena + pl.dst_base);
   unsigned long long* dH = dB + W * ds;
   unsigned int* dM = reinterpret_cast<unsigned int*>(dH + ds);
-  unsigned char* dN = reinterpret_cast<unsigned char*>(dM + ds);
   const unsigned int t = pl.t, L = p.L;
   const unsigned long long s = pl.s;
   // a two-level step has t + 1 < L': the children are within the bound
@@ -557,16 +552,13 @@ __device__ __forceinline__ void process_bitset_fused_lane(const EngineParams& p,
             const unsigned int w = 64u * q + __ffsll((long long)g) - 1;
             g &= g - 1;
             if (slot < ds) {
-              unsigned int nc = 0;
 #pragma unroll
               for (int r = 0; r < W; ++r) {
                 dB[r * ds + slot] = nb2[r];
-                if (next_ok) nc += __popcll(adj[(unsigned long long)w * W + r] & ~nb2[r] & ~a1[r]);
+                if (next_ok) nx += __popcll(adj[(unsigned long long)w * W + r] & ~nb2[r] & ~a1[r]);
               }
               dH[slot] = hv + rtab[w];
               dM[slot] = v1 | (w << 16);
-              dN[slot] = (unsigned char)nc;
-              nx += nc;
             } else {
               set_err(p.ctl, kDevBounds, 5);
             }
@@ -631,21 +623,20 @@ __device__ __forceinline__ void process_bitset_flat(const EngineParams& p, const
   unsigned long long* dB = reinterpret_cast<unsigned long long*>(p.arena + pl.dst_base);
   unsigned long long* dH = dB + W * ds;
   unsigned int* dM = reinterpret_cast<unsigned int*>(dH + ds);
-  unsigned char* dN = reinterpret_cast<unsigned char*>(dM + ds);
-  const unsigned char* sN = reinterpret_cast<const unsigned char*>(sM + ss);
   const bool store = ds != 0;
   const unsigned int t = pl.t, L = p.L;
   const unsigned long long s = pl.s;
   const bool close_ok = t + 1 <= L, next_ok = t + 2 < L;
   const unsigned long long gam = (unsigned long long)(t + 1) * kGamma;
   unsigned long long nx = 0, ncyc = 0, hacc = 0;
+  const unsigned long long T = (unsigned long long)gridDim.x * blockDim.x;
+  const unsigned long long gwarp = ((unsigned long long)wid * gridDim.x + blockIdx.x) * 32ull;
 
   // list the set bits of m[j][k] (j < P, k < W), the children of the staged paths, as
   // entries, CL at a time, and write each chunk out with one entry per lane.  The warp's
   // slots come from one atomic, issued before the listing so that its round trip overlaps
   // it; lane i writes slot base + c0 + i, so each plane is stored contiguously.
   unsigned long long m[P][W];
-  unsigned long long cnext = 0, cend_slot = 0;  // the chunk's reserved child slots (warp-uniform)
   auto list_children = [&]() {
     unsigned int cnt = 0;
 #pragma unroll
@@ -660,8 +651,8 @@ __device__ __forceinline__ void process_bitset_flat(const EngineParams& p, const
     }
     const unsigned int excl = incl - cnt, total = __shfl_sync(0xffffffffu, incl, 31);
     if (total == 0) return;
-    const unsigned long long base = cnext;  // the next slots of the chunk's range
-    cnext += total;
+    unsigned long long base = 0;
+    if (lane == 0) base = atomicAdd(&p.ctl->cnt[s % 3], (unsigned long long)total);
     for (unsigned int c0 = 0; c0 < total; c0 += CL) {
       if (cnt && excl < c0 + CL && excl + cnt > c0) {
         unsigned int idx = excl;
@@ -679,24 +670,21 @@ __device__ __forceinline__ void process_bitset_flat(const EngineParams& p, const
           }
       }
       __syncwarp();
-      const unsigned long long b0 = base + c0;
+      const unsigned long long b0 = __shfl_sync(0xffffffffu, base, 0) + c0;
       const unsigned int n = min(CL, total - c0);
       for (unsigned int i = lane; i < n; i += 32) {
         const unsigned int e = sl[i], pj = e >> 8, v = e & 0xFFu;
         const unsigned long long slot = b0 + i;
         if (slot < ds) {
           const unsigned int v1 = sv1[pj];
-          unsigned int nc = 0;
 #pragma unroll
           for (int q = 0; q < W; ++q) {
             const unsigned long long nb = snb[pj * W + q];
             dB[q * ds + slot] = nb;
-            if (next_ok) nc += __popcll(adj[(unsigned long long)v * W + q] & ~nb & ~adj[(unsigned long long)v1 * W + q]);
+            if (next_ok) nx += __popcll(adj[(unsigned long long)v * W + q] & ~nb & ~adj[(unsigned long long)v1 * W + q]);
           }
           dH[slot] = sh[pj] + rtab[v];
           dM[slot] = v1 | (v << 16);
-          dN[slot] = (unsigned char)nc;
-          nx += nc;
         } else {
           set_err(p.ctl, kDevBounds, 1);
         }
@@ -705,38 +693,14 @@ __device__ __forceinline__ void process_bitset_flat(const EngineParams& p, const
     }
   };
 
-  // Work distribution: a warp takes contiguous chunks of the step's records from a step
-  // counter, and reserves the child slots of a whole chunk with one atomic from the child
-  // counts the records carry (a single counter taking one atomic per round of every warp
-  // was the grid's hot spot); rounds of pf * 32 consecutive records
   const unsigned int pf = p.pf >= 1 && p.pf <= (unsigned)P ? p.pf : (unsigned)P;
-  const unsigned int RW = pf * 32;
-  const unsigned long long ntot = pl.end - pl.begin;
-  const unsigned long long nwarps = (unsigned long long)gridDim.x * (NT / 32);
-  unsigned long long chunk = (ntot / (nwarps * 8) + RW - 1) / RW * RW;
-  chunk = chunk < RW ? RW : (chunk > 16ull * RW ? 16ull * RW : chunk);
-  for (;;) {
-  unsigned long long cs = 0;
-  if (lane == 0) cs = atomicAdd(&p.ctl->take[s % 3], chunk);
-  cs = __shfl_sync(0xffffffffu, cs, 0);
-  if (cs >= ntot) break;
-  const unsigned long long cend = pl.begin + min(cs + chunk, ntot);
-  if (store) {
-    unsigned int nch = 0;
-    for (unsigned long long i = pl.begin + cs + lane; i < cend; i += 32) nch += ldcg8(sN + i);
-    nch = __reduce_add_sync(0xffffffffu, nch);
-    unsigned long long b = 0;
-    if (lane == 0 && nch) b = atomicAdd(&p.ctl->cnt[s % 3], (unsigned long long)nch);
-    cnext = __shfl_sync(0xffffffffu, b, 0);
-    cend_slot = cnext + nch;
-  }
-  for (unsigned long long wb = pl.begin + cs; wb < cend; wb += RW) {
+  for (unsigned long long wb = pl.begin + gwarp; wb < pl.end; wb += pf * T) {
     const unsigned long long t0 = wb + lane;
     unsigned long long cm[P][W];
 #pragma unroll
     for (int j = 0; j < P; ++j) {
-      const unsigned long long i = t0 + (unsigned long long)j * 32ull;
-      const bool valid = (unsigned)j < pf && i < cend;
+      const unsigned long long i = t0 + (unsigned long long)j * T;
+      const bool valid = (unsigned)j < pf && i < pl.end;
       unsigned long long B[W];
 #pragma unroll
       for (int k = 0; k < W; ++k) B[k] = valid ? ldcg64(sB + k * ss + i) : ~0ull;
@@ -773,9 +737,6 @@ __device__ __forceinline__ void process_bitset_flat(const EngineParams& p, const
         }
       }
     if (store) list_children();
-  }
-  // (the children listed equal the child counts the records carry)
-  if (store && cnext != cend_slot && lane == 0) set_err(p.ctl, kDevBounds, 7);
   }
   block_sum3_u64(nx, ncyc, hacc, s_red);
   if (tid == 0) {
@@ -828,7 +789,6 @@ __device__ __forceinline__ void process_bitset_fused(const EngineParams& p, cons
   unsigned long long* dB = reinterpret_cast<unsigned long long*>(p.arena + pl.dst_base);
   unsigned long long* dH = dB + W * ds;
   unsigned int* dM = reinterpret_cast<unsigned int*>(dH + ds);
-  unsigned char* dN = reinterpret_cast<unsigned char*>(dM + ds);
   const unsigned int t = pl.t, L = p.L;
   const unsigned long long s = pl.s;
   // level t+1 is stored in the single-level form (t+1 < L' holds for a fused step)
@@ -886,18 +846,15 @@ __device__ __forceinline__ void process_bitset_fused(const EngineParams& p, cons
         const unsigned long long slot = b0 + i;
         if (slot < ds) {
           const unsigned int v1 = sv12[c];
-          unsigned int nc = 0;
 #pragma unroll
           for (int q = 0; q < W; ++q) {
             const unsigned long long nb = snb2[c * W + q];
             dB[q * ds + slot] = nb;
             if (next_ok)
-              nc += __popcll(adj[(unsigned long long)w * W + q] & ~nb & ~adj[(unsigned long long)v1 * W + q]);
+              nx += __popcll(adj[(unsigned long long)w * W + q] & ~nb & ~adj[(unsigned long long)v1 * W + q]);
           }
           dH[slot] = sh2[c] + rtab[w];
           dM[slot] = v1 | (w << 16);
-          dN[slot] = (unsigned char)nc;
-          nx += nc;
         } else {
           set_err(p.ctl, kDevBounds, 4);
         }

@@ -10,13 +10,12 @@
 // depth-first before the next chunk (bounded frontier).
 //
 // Record formats (one path per record):
-//   bitset, one graph, W = ceil(n/64) words:  B[W] (u64 planes), H (u64), M (u32), N (u8)
+//   bitset, one graph, W = ceil(n/64) words:  B[W] (u64 planes), H (u64), M (u32)
 //       B  blocked set: union of Adj(v_i) over the interior v_2..v_{t-1}, plus every
 //          vertex whose label is <= l(v_2).  A candidate v of Adj(v_t) passes the label
 //          test and the chord test of Algorithm 3 iff v is not in B.
 //       H  sum of r(original id) over the path's vertices (running cycle-hash input).
 //       M  v_1 | v_t << 16 (relabelled ids).
-//       N  (u8) the path's exact number of children (0 when they would reach L').
 //   bitset, many graphs (n <= 64, W = 1): same planes, M = v1 | vt<<6 | t<<12 | slot<<18,
 //       and N (u8): the path's exact number of children (0 when they would reach L').
 //   CSR, one graph: one record per path, its relabelled u16 ids in order padded with 0xFFFF
@@ -477,9 +476,9 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned 
 __host__ __device__ __forceinline__ unsigned long long round_up(unsigned long long x, unsigned long long a) {
   return (x + a - 1) / a * a;
 }
-// Record bytes: bitset planes (8W + 13), CSR records (2 csr_rec_u16(t)).
+// Record bytes: bitset planes (8W + 12), CSR records (2 csr_rec_u16(t)).
 __host__ __device__ __forceinline__ unsigned long long bitset_region_bytes(unsigned long long stride, int W) {
-  return round_up(stride * (8ull * W + 13ull), 256);
+  return round_up(stride * (8ull * W + 12ull), 256);
 }
 // Batch records: B, H (u64 planes), M (u32 plane) and N (u8 plane), 21 bytes.
 __host__ __device__ __forceinline__ unsigned long long multi_region_bytes(unsigned long long stride) {

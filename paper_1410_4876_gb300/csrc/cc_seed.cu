@@ -348,7 +348,6 @@ __global__ void __launch_bounds__(256) seed_bitset_kernel(EngineParams p, unsign
     unsigned long long* dB = (unsigned long long*)p.arena;
     unsigned long long* dH = dB + (unsigned long long)W * stride;
     unsigned int* dM = (unsigned int*)(dH + stride);
-    unsigned char* dN = (unsigned char*)(dM + stride);
     unsigned long long slot = base;
 #pragma unroll
     for (int k = 0; k < W; ++k) {
@@ -361,13 +360,10 @@ __global__ void __launch_bounds__(256) seed_bitset_kernel(EngineParams p, unsign
         for (int q = 0; q < W; ++q) dB[(unsigned long long)q * stride + slot] = B[q];
         dH[slot] = H0 + rtab[y];
         dM[slot] = x | (y << 16);
-        unsigned int nc = 0;  // the triplet's exact child count
         if (L > 4) {
 #pragma unroll
-          for (int q = 0; q < W; ++q) nc += __popcll(adj[(unsigned long long)y * W + q] & ~B[q] & ~ax[q]);
+          for (int q = 0; q < W; ++q) nx += __popcll(adj[(unsigned long long)y * W + q] & ~B[q] & ~ax[q]);
         }
-        dN[slot] = (unsigned char)nc;
-        nx += nc;
         ++slot;
       }
     }
