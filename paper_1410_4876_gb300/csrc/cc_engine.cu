@@ -1000,6 +1000,9 @@ __device__ __forceinline__ void process_multi_flat(const EngineParams& p, const 
   __shared__ FlatSmem<1, P, NT> fs;
   __shared__ unsigned long long s_gadj[NT / 32][64];
   __shared__ unsigned long long s_grt[NT / 32][64];
+  __shared__ unsigned long long s_rb[NT / 32][2][P * 32];  // records of this round and the next
+  __shared__ unsigned long long s_rh[NT / 32][2][P * 32];
+  __shared__ unsigned int s_rm[NT / 32][2][P * 32];
   const unsigned int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   unsigned long long* snb = fs.nb[wid];
   unsigned long long* sh = fs.h[wid];
@@ -1125,9 +1128,9 @@ __device__ __forceinline__ void process_multi_flat(const EngineParams& p, const 
   const unsigned int RW = pf * 32;  // records per warp round
   const unsigned long long total = pl.end - pl.begin;
   const unsigned long long nwarps = (unsigned long long)gridDim.x * (NT / 32);
-  // chunks of about an eighth of a warp's share, between 1 and 16 rounds
-  unsigned long long chunk = (total / (nwarps * 8) + RW - 1) / RW * RW;
-  chunk = chunk < RW ? RW : (chunk > 16ull * RW ? 16ull * RW : chunk);
+  // chunks of about a quarter of a warp's share, between 1 and 32 rounds
+  unsigned long long chunk = (total / (nwarps * 4) + RW - 1) / RW * RW;
+  chunk = chunk < RW ? RW : (chunk > 32ull * RW ? 32ull * RW : chunk);
   for (;;) {
     unsigned long long c0 = 0;
     if (lane == 0) c0 = atomicAdd(&p.ctl->take[s % 3], chunk);
@@ -1144,9 +1147,28 @@ __device__ __forceinline__ void process_multi_flat(const EngineParams& p, const 
       cnext = __shfl_sync(0xffffffffu, b, 0);
       cend_slot = cnext + nch;
     }
-    for (unsigned long long wb = pl.begin + c0; wb < cend; wb += RW) {
+    // the records of a round are copied into this warp's shared memory by cp.async while
+    // the round before is expanded (each lane copies, then reads, its own records)
+    auto prefetch = [&](unsigned long long w0, unsigned int buf) {
+#pragma unroll
+      for (int j = 0; j < P; ++j) {
+        const unsigned long long i = w0 + lane + (unsigned long long)j * 32ull;
+        if ((unsigned)j < pf && i < cend) {
+          cp_async8(&s_rb[wid][buf][j * 32 + lane], sB + i);
+          cp_async8(&s_rh[wid][buf][j * 32 + lane], sH + i);
+          cp_async4(&s_rm[wid][buf][j * 32 + lane], sM + i);
+        }
+      }
+      cp_async_commit();
+    };
+    unsigned int buf = 0;
+    prefetch(pl.begin + c0, 0);
+    for (unsigned long long wb = pl.begin + c0; wb < cend; wb += RW, buf ^= 1u) {
+      if (wb + RW < cend) prefetch(wb + RW, buf ^ 1u);
+      else cp_async_commit();  // (an empty group: the wait below still means "this round")
+      cp_async_wait_1();
       // the graph of the round's first record (always valid): stage it if it changed
-      const unsigned int g0 = ldcg32(sM + wb) >> 18;
+      const unsigned int g0 = __shfl_sync(0xffffffffu, s_rm[wid][buf][lane], 0) >> 18;
       if (g0 != cg) {
         __syncwarp();
         ga[lane] = __ldg(adj + (unsigned long long)g0 * 64ull + lane);
@@ -1164,9 +1186,9 @@ __device__ __forceinline__ void process_multi_flat(const EngineParams& p, const 
       for (int j = 0; j < P; ++j) {
         const unsigned long long i = t0 + (unsigned long long)j * 32ull;
         const bool valid = (unsigned)j < pf && i < cend;
-        const unsigned long long B = valid ? ldcg64(sB + i) : ~0ull;
-        const unsigned long long H = valid ? ldcg64(sH + i) : 0ull;
-        const unsigned int M = valid ? ldcg32(sM + i) : 0u;
+        const unsigned long long B = valid ? s_rb[wid][buf][j * 32 + lane] : ~0ull;
+        const unsigned long long H = valid ? s_rh[wid][buf][j * 32 + lane] : 0ull;
+        const unsigned int M = valid ? s_rm[wid][buf][j * 32 + lane] : 0u;
         const unsigned int v1 = M & 63u, vt = (M >> 6) & 63u, tt = (M >> 12) & 63u, g = M >> 18;
         const unsigned int Lr = valid ? (g == cg ? cL : p.Lg[g]) : 0u;
         const unsigned long long at = A(g, vt), a1 = A(g, v1);

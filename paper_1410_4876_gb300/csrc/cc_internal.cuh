@@ -455,6 +455,17 @@ __device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, unsign
       "l"(src), "r"(bytes), "r"(smem_addr(bar))
       : "memory");
 }
+// Asynchronous per-thread copies global -> shared (cp.async, no registers held while in
+// flight); a thread waits for its own earlier groups with cp_async_wait_1.
+__device__ __forceinline__ void cp_async8(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+// every group but the most recent one has landed
+__device__ __forceinline__ void cp_async_wait_1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 // L2 prefetch of a contiguous global range by the bulk-copy engine (no registers, no
 // shared memory); address and size are multiples of 16 bytes.
 __device__ __forceinline__ void bulk_prefetch_l2(const void* src, unsigned int bytes) {
