@@ -25,7 +25,8 @@ namespace cc {
 // minima of supergroup s (n <= 32768 gives at most 32 supergroups, one per lane).
 //
 // Each step of the labelling (Section 2: remove a vertex of minimum current degree, ties
-// by smallest id) is one warp reduction over sgmin.  Removing u lowers its neighbours'
+// by smallest id) is one warp reduction over sgmin (over gmin directly when there are at
+// most 64 groups).  Removing u lowers its neighbours'
 // keys, and only keys of u's own group and supergroup can rise (u's key becomes dead), so
 // a step recomputes gmin of u's group (one load per lane: the group's keys, with the
 // neighbours' new keys folded in) and sgmin of u's supergroup (one load per lane), and
@@ -74,8 +75,13 @@ __global__ void __launch_bounds__(1024) label_single_kernel(const unsigned int* 
       sgmin[lane] = m;  // (lanes past the last supergroup hold dead)
     }
     __syncwarp();
+    // up to 64 groups (n <= 2048): the step's minimum straight from the group minima, two
+    // per lane, and no supergroup level to keep
+    const bool flat = G <= 64;
     for (unsigned int i = 0; i < n; ++i) {
-      const unsigned int m = __reduce_min_sync(0xffffffffu, sgmin[lane]);
+      const unsigned int m = flat ? __reduce_min_sync(0xffffffffu, min(lane < G ? gmin[lane] : kDead,
+                                                                       lane + 32 < G ? gmin[lane + 32] : kDead))
+                                  : __reduce_min_sync(0xffffffffu, sgmin[lane]);
       const unsigned int u = m & 0xFFFFu, gu = u >> 5, su = gu >> 5;
       // u's group without u, and u's row (loaded side by side)
       const unsigned int v = gu * 32 + lane;
@@ -92,7 +98,7 @@ __global__ void __launch_bounds__(1024) label_single_kernel(const unsigned int* 
             kg = min(kg, kw);
           } else {
             atomicMin(&gmin[gw], kw);
-            if ((gw >> 5) != su) atomicMin(&sgmin[gw >> 5], kw);
+            if (!flat && (gw >> 5) != su) atomicMin(&sgmin[gw >> 5], kw);
           }
         }
       }
@@ -104,11 +110,13 @@ __global__ void __launch_bounds__(1024) label_single_kernel(const unsigned int* 
         newid[u] = i;
       }
       __syncwarp();
-      // u's supergroup: its groups' minima after this step's updates
-      const unsigned int g2 = su * 32 + lane;
-      const unsigned int ks = __reduce_min_sync(0xffffffffu, g2 < G ? gmin[g2] : kDead);
-      if (lane == 0) sgmin[su] = ks;
-      __syncwarp();
+      if (!flat) {
+        // u's supergroup: its groups' minima after this step's updates
+        const unsigned int g2 = su * 32 + lane;
+        const unsigned int ks = __reduce_min_sync(0xffffffffu, g2 < G ? gmin[g2] : kDead);
+        if (lane == 0) sgmin[su] = ks;
+        __syncwarp();
+      }
     }
   }
   __syncthreads();
