@@ -204,7 +204,9 @@ __device__ bool plan_step(const EngineParams& p, LocalState& st, StepPlan& pl) {
     // the division is only needed when the level does not fit (the common case is a
     // multiply-compare)
     const bool fits = freeb > 1024 && (round_up(cap, 8) + 8) * rb <= freeb - 1024;
-    const unsigned long long maxcap = fits ? cap : (freeb > 1024 ? ((freeb - 1024) / rb) & ~7ull : 0ull);
+    unsigned long long maxcap = fits ? cap : (freeb > 1024 ? ((freeb - 1024) / rb) & ~7ull : 0ull);
+    // (batch frames hold fewer than 2^32 records: the batch form indexes them with 32 bits)
+    if constexpr (KindTraits<K>::multi) maxcap = min(maxcap, 0xFFFF0000ull);
     if (cap > maxcap) {
       // Spill: this chunk's subtree runs depth-first before the rest of the frame, and
       // each deeper stored level of that subtree needs room too, so the chunk's children
@@ -1015,13 +1017,16 @@ __device__ __forceinline__ void process_multi_flat(const EngineParams& p, const 
   const unsigned long long* sH = sB + ss;
   const unsigned int* sM = reinterpret_cast<const unsigned int*>(sH + ss);
   const unsigned char* sN = reinterpret_cast<const unsigned char*>(sM + ss);
+  // (record indices below are relative to the step's first record and to the child region:
+  // 32 bits, as the planner keeps batch frames under 2^32 records)
   unsigned long long* dB = reinterpret_cast<unsigned long long*>(p.arena + pl.dst_base);
   unsigned long long* dH = dB + ds;
   unsigned int* dM = reinterpret_cast<unsigned int*>(dH + ds);
   unsigned char* dN = reinterpret_cast<unsigned char*>(dM + ds);
   const bool store = ds != 0;
+  const unsigned int ds32 = (unsigned int)min(ds, 0xFFFFFFFFull);
   const unsigned long long s = pl.s;
-  unsigned long long nx = 0;
+  unsigned int nx = 0;  // children of this lane's stored children (fits 32 bits per lane and step)
   StatRun run;
   run.key = 0xFFFFFFFFu;
   unsigned long long hacc = 0;      // closing hashes of slot hkey, per lane
@@ -1041,14 +1046,13 @@ __device__ __forceinline__ void process_multi_flat(const EngineParams& p, const 
   };
 
   // children entries [0, n) take slots base + [0, n)
-  auto flush_children = [&](unsigned int n, unsigned long long base) {
+  auto flush_children = [&](unsigned int n, unsigned int base) {
     __syncwarp();
-    base = __shfl_sync(0xffffffffu, base, 0);
     for (unsigned int i = lane; i < n; i += 32) {
       const unsigned int e = sl[i], pj = e >> 8, v = e & 0xFFu;
       const unsigned int meta = smeta[pj], v1 = meta & 63u, tt = (meta >> 6) & 63u, g = (meta >> 12) & 0x7FFFFu;
-      const unsigned long long slot = base + i;
-      if (slot < ds) {
+      const unsigned int slot = base + i;
+      if (slot < ds32) {
         const unsigned long long nb = snb[pj];
         dB[slot] = nb;
         dH[slot] = sh[pj] + R(g, v);
@@ -1090,7 +1094,7 @@ __device__ __forceinline__ void process_multi_flat(const EngineParams& p, const 
     __syncwarp();
   };
   unsigned long long m[P];
-  unsigned long long cnext = 0, cend_slot = 0;  // the chunk's reserved child slots (warp-uniform)
+  unsigned int cnext = 0, cend_slot = 0;  // the chunk's reserved child slots (warp-uniform)
   auto list_and_work = [&](bool children) {
     unsigned int cnt = 0;
 #pragma unroll
@@ -1103,7 +1107,7 @@ __device__ __forceinline__ void process_multi_flat(const EngineParams& p, const 
     }
     const unsigned int excl = incl - cnt, total = __shfl_sync(0xffffffffu, incl, 31);
     // a round's children take the next slots of the chunk's reserved range
-    const unsigned long long base = cnext;
+    const unsigned int base = cnext;
     if (children) cnext += total;
     for (unsigned int c0 = 0; c0 < total; c0 += CL) {
       if (cnt && excl < c0 + CL && excl + cnt > c0) {
@@ -1126,44 +1130,50 @@ __device__ __forceinline__ void process_multi_flat(const EngineParams& p, const 
 
   const unsigned int pf = p.pf >= 1 && p.pf <= (unsigned)P ? p.pf : (unsigned)P;
   const unsigned int RW = pf * 32;  // records per warp round
-  const unsigned long long total = pl.end - pl.begin;
-  const unsigned long long nwarps = (unsigned long long)gridDim.x * (NT / 32);
+  const unsigned int total = (unsigned int)(pl.end - pl.begin);  // (below 2^32, see plan_step)
+  const unsigned int nwarps = gridDim.x * (NT / 32);
   // chunks of about a quarter of a warp's share, between 1 and 32 rounds
-  unsigned long long chunk = (total / (nwarps * 4) + RW - 1) / RW * RW;
-  chunk = chunk < RW ? RW : (chunk > 32ull * RW ? 32ull * RW : chunk);
+  unsigned int chunk = (total / (nwarps * 4) + RW - 1) / RW * RW;
+  chunk = chunk < RW ? RW : (chunk > 32u * RW ? 32u * RW : chunk);
+  // the step's records, indexed from its first one
+  const unsigned long long* sB0 = sB + pl.begin;
+  const unsigned long long* sH0 = sH + pl.begin;
+  const unsigned int* sM0 = sM + pl.begin;
+  const unsigned char* sN0 = sN + pl.begin;
   for (;;) {
-    unsigned long long c0 = 0;
-    if (lane == 0) c0 = atomicAdd(&p.ctl->take[s % 3], chunk);
-    c0 = __shfl_sync(0xffffffffu, c0, 0);
-    if (c0 >= total) break;
-    const unsigned long long cend = pl.begin + min(c0 + chunk, total);
+    unsigned long long c64 = 0;
+    if (lane == 0) c64 = atomicAdd(&p.ctl->take[s % 3], (unsigned long long)chunk);
+    c64 = __shfl_sync(0xffffffffu, c64, 0);
+    if (c64 >= total) break;
+    const unsigned int c0 = (unsigned int)c64;
+    const unsigned int cend = min(c0 + chunk, total);
     // the chunk's children (the records' exact child counts) take one range of slots
     if (store) {
       unsigned int nch = 0;
-      for (unsigned long long i = pl.begin + c0 + lane; i < cend; i += 32) nch += ldcg8(sN + i);
+      for (unsigned int i = c0 + lane; i < cend; i += 32) nch += ldcg8(sN0 + i);
       nch = __reduce_add_sync(0xffffffffu, nch);
       unsigned long long b = 0;
       if (lane == 0 && nch) b = atomicAdd(&p.ctl->cnt[s % 3], (unsigned long long)nch);
-      cnext = __shfl_sync(0xffffffffu, b, 0);
+      cnext = (unsigned int)__shfl_sync(0xffffffffu, b, 0);
       cend_slot = cnext + nch;
     }
     // the records of a round are copied into this warp's shared memory by cp.async while
     // the round before is expanded (each lane copies, then reads, its own records)
-    auto prefetch = [&](unsigned long long w0, unsigned int buf) {
+    auto prefetch = [&](unsigned int w0, unsigned int buf) {
 #pragma unroll
       for (int j = 0; j < P; ++j) {
-        const unsigned long long i = w0 + lane + (unsigned long long)j * 32ull;
+        const unsigned int i = w0 + lane + j * 32u;
         if ((unsigned)j < pf && i < cend) {
-          cp_async8(&s_rb[wid][buf][j * 32 + lane], sB + i);
-          cp_async8(&s_rh[wid][buf][j * 32 + lane], sH + i);
-          cp_async4(&s_rm[wid][buf][j * 32 + lane], sM + i);
+          cp_async8(&s_rb[wid][buf][j * 32 + lane], sB0 + i);
+          cp_async8(&s_rh[wid][buf][j * 32 + lane], sH0 + i);
+          cp_async4(&s_rm[wid][buf][j * 32 + lane], sM0 + i);
         }
       }
       cp_async_commit();
     };
     unsigned int buf = 0;
-    prefetch(pl.begin + c0, 0);
-    for (unsigned long long wb = pl.begin + c0; wb < cend; wb += RW, buf ^= 1u) {
+    prefetch(c0, 0);
+    for (unsigned int wb = c0; wb < cend; wb += RW, buf ^= 1u) {
       if (wb + RW < cend) prefetch(wb + RW, buf ^ 1u);
       else cp_async_commit();  // (an empty group: the wait below still means "this round")
       cp_async_wait_1();
@@ -1179,12 +1189,12 @@ __device__ __forceinline__ void process_multi_flat(const EngineParams& p, const 
         cg = g0;
         __syncwarp();
       }
-      const unsigned long long t0 = wb + lane;
+      const unsigned int t0 = wb + lane;
       unsigned long long ch[P];
       unsigned int key[P], nc[P], nk[P];
 #pragma unroll
       for (int j = 0; j < P; ++j) {
-        const unsigned long long i = t0 + (unsigned long long)j * 32ull;
+        const unsigned int i = t0 + j * 32u;
         const bool valid = (unsigned)j < pf && i < cend;
         const unsigned long long B = valid ? s_rb[wid][buf][j * 32 + lane] : ~0ull;
         const unsigned long long H = valid ? s_rh[wid][buf][j * 32 + lane] : 0ull;
@@ -1243,7 +1253,7 @@ __device__ __forceinline__ void process_multi_flat(const EngineParams& p, const 
   }
   flush_hash();
   run.flush(p, s);
-  const unsigned long long tot = warp_sum_u64(nx);
+  const unsigned long long tot = warp_sum_u64((unsigned long long)nx);
   if (lane == 0 && tot) atomicAdd(&p.ctl->nxt[s % 3], tot);
 }
 
