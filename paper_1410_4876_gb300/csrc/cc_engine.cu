@@ -205,8 +205,9 @@ __device__ bool plan_step(const EngineParams& p, LocalState& st, StepPlan& pl) {
     // multiply-compare)
     const bool fits = freeb > 1024 && (round_up(cap, 8) + 8) * rb <= freeb - 1024;
     unsigned long long maxcap = fits ? cap : (freeb > 1024 ? ((freeb - 1024) / rb) & ~7ull : 0ull);
-    // (batch frames hold fewer than 2^32 records: the batch form indexes them with 32 bits)
-    if constexpr (KindTraits<K>::multi) maxcap = min(maxcap, 0xFFFF0000ull);
+    // (bitset and batch frames hold fewer than 2^32 records: their forms index them with 32
+    // bits)
+    if constexpr (!KindTraits<K>::csr) maxcap = min(maxcap, 0xFFFF0000ull);
     if (cap > maxcap) {
       // Spill: this chunk's subtree runs depth-first before the rest of the frame, and
       // each deeper stored level of that subtree needs room too, so the chunk's children
@@ -630,9 +631,17 @@ __device__ __forceinline__ void process_bitset_flat(const EngineParams& p, const
   const unsigned long long s = pl.s;
   const bool close_ok = t + 1 <= L, next_ok = t + 2 < L;
   const unsigned long long gam = (unsigned long long)(t + 1) * kGamma;
-  unsigned long long nx = 0, ncyc = 0, hacc = 0;
-  const unsigned long long T = (unsigned long long)gridDim.x * blockDim.x;
-  const unsigned long long gwarp = ((unsigned long long)wid * gridDim.x + blockIdx.x) * 32ull;
+  unsigned long long hacc = 0;
+  unsigned int nx = 0, ncyc = 0;  // per lane and step: 32 bits
+  // (record indices relative to the step's first record and the child region: 32 bits, as
+  // the planner keeps bitset frames under 2^32 records)
+  const unsigned int ds32 = (unsigned int)min(ds, 0xFFFFFFFFull);
+  const unsigned int nrec = (unsigned int)(pl.end - pl.begin);
+  const unsigned long long* sB0 = sB + pl.begin;
+  const unsigned long long* sH0 = sH + pl.begin;
+  const unsigned int* sM0 = sM + pl.begin;
+  const unsigned int T = gridDim.x * blockDim.x;
+  const unsigned int gwarp = (wid * gridDim.x + blockIdx.x) * 32u;
 
   // list the set bits of m[j][k] (j < P, k < W), the children of the staged paths, as
   // entries, CL at a time, and write each chunk out with one entry per lane.  The warp's
@@ -655,6 +664,7 @@ __device__ __forceinline__ void process_bitset_flat(const EngineParams& p, const
     if (total == 0) return;
     unsigned long long base = 0;
     if (lane == 0) base = atomicAdd(&p.ctl->cnt[s % 3], (unsigned long long)total);
+    const unsigned int base32 = (unsigned int)__shfl_sync(0xffffffffu, base, 0);
     for (unsigned int c0 = 0; c0 < total; c0 += CL) {
       if (cnt && excl < c0 + CL && excl + cnt > c0) {
         unsigned int idx = excl;
@@ -672,12 +682,12 @@ __device__ __forceinline__ void process_bitset_flat(const EngineParams& p, const
           }
       }
       __syncwarp();
-      const unsigned long long b0 = __shfl_sync(0xffffffffu, base, 0) + c0;
+      const unsigned int b0 = base32 + c0;
       const unsigned int n = min(CL, total - c0);
       for (unsigned int i = lane; i < n; i += 32) {
         const unsigned int e = sl[i], pj = e >> 8, v = e & 0xFFu;
-        const unsigned long long slot = b0 + i;
-        if (slot < ds) {
+        const unsigned int slot = b0 + i;
+        if (slot < ds32) {
           const unsigned int v1 = sv1[pj];
 #pragma unroll
           for (int q = 0; q < W; ++q) {
@@ -696,18 +706,18 @@ __device__ __forceinline__ void process_bitset_flat(const EngineParams& p, const
   };
 
   const unsigned int pf = p.pf >= 1 && p.pf <= (unsigned)P ? p.pf : (unsigned)P;
-  for (unsigned long long wb = pl.begin + gwarp; wb < pl.end; wb += pf * T) {
-    const unsigned long long t0 = wb + lane;
+  for (unsigned int wb = gwarp; wb < nrec; wb += pf * T) {
+    const unsigned int t0 = wb + lane;
     unsigned long long cm[P][W];
 #pragma unroll
     for (int j = 0; j < P; ++j) {
-      const unsigned long long i = t0 + (unsigned long long)j * T;
-      const bool valid = (unsigned)j < pf && i < pl.end;
+      const unsigned int i = t0 + j * T;
+      const bool valid = (unsigned)j < pf && i < nrec;
       unsigned long long B[W];
 #pragma unroll
-      for (int k = 0; k < W; ++k) B[k] = valid ? ldcg64(sB + k * ss + i) : ~0ull;
-      const unsigned long long H = valid ? ldcg64(sH + i) : 0ull;
-      const unsigned int M = valid ? ldcg32(sM + i) : 0u;
+      for (int k = 0; k < W; ++k) B[k] = valid ? ldcg64(sB0 + k * ss + i) : ~0ull;
+      const unsigned long long H = valid ? ldcg64(sH0 + i) : 0ull;
+      const unsigned int M = valid ? ldcg32(sM0 + i) : 0u;
       const unsigned int v1 = M & 0xFFFFu, vt = M >> 16;
       const unsigned int pj = j * 32 + lane;
 #pragma unroll
@@ -740,10 +750,11 @@ __device__ __forceinline__ void process_bitset_flat(const EngineParams& p, const
       }
     if (store) list_children();
   }
-  block_sum3_u64(nx, ncyc, hacc, s_red);
+  unsigned long long nx64 = nx, ncyc64 = ncyc;
+  block_sum3_u64(nx64, ncyc64, hacc, s_red);
   if (tid == 0) {
-    if (nx) atomicAdd(&p.ctl->nxt[s % 3], nx);
-    if (ncyc) atomicAdd(&p.hist[t + 1], ncyc);
+    if (nx64) atomicAdd(&p.ctl->nxt[s % 3], nx64);
+    if (ncyc64) atomicAdd(&p.hist[t + 1], ncyc64);
     if (hacc) atomicAdd(p.hash, hacc);
   }
 }
@@ -796,9 +807,17 @@ __device__ __forceinline__ void process_bitset_fused(const EngineParams& p, cons
   // level t+1 is stored in the single-level form (t+1 < L' holds for a fused step)
   const bool close2_ok = t + 2 <= L, store2 = ds != 0, next_ok = t + 3 < L;
   const unsigned long long gam1 = (unsigned long long)(t + 1) * kGamma, gam2 = (unsigned long long)(t + 2) * kGamma;
-  unsigned long long nx = 0, ncyc1 = 0, ncyc2 = 0, hacc = 0;
-  const unsigned long long T = (unsigned long long)gridDim.x * blockDim.x;
-  const unsigned long long gwarp = ((unsigned long long)wid * gridDim.x + blockIdx.x) * 32ull;
+  unsigned long long hacc = 0;
+  unsigned int nx = 0, ncyc1 = 0, ncyc2 = 0;  // per lane and step: 32 bits
+  // (record indices relative to the step's first record and the child region: 32 bits, as
+  // the planner keeps bitset frames under 2^32 records)
+  const unsigned int ds32 = (unsigned int)min(ds, 0xFFFFFFFFull);
+  const unsigned int nrec = (unsigned int)(pl.end - pl.begin);
+  const unsigned long long* sB0 = sB + pl.begin;
+  const unsigned long long* sH0 = sH + pl.begin;
+  const unsigned int* sM0 = sM + pl.begin;
+  const unsigned int T = gridDim.x * blockDim.x;
+  const unsigned int gwarp = (wid * gridDim.x + blockIdx.x) * 32u;
 
   auto scan = [&](unsigned int cnt, unsigned int& excl, unsigned int& total) {
     unsigned int incl = cnt;
@@ -824,6 +843,7 @@ __device__ __forceinline__ void process_bitset_fused(const EngineParams& p, cons
     if (total == 0) return;
     unsigned long long base = 0;
     if (lane == 0) base = atomicAdd(&p.ctl->cnt[s % 3], (unsigned long long)total);
+    const unsigned int base32 = (unsigned int)__shfl_sync(0xffffffffu, base, 0);
     for (unsigned int c0 = 0; c0 < total; c0 += CL2) {
       if (cnt && excl < c0 + CL2 && excl + cnt > c0) {
         unsigned int idx = excl;
@@ -841,12 +861,12 @@ __device__ __forceinline__ void process_bitset_fused(const EngineParams& p, cons
           }
       }
       __syncwarp();
-      const unsigned long long b0 = __shfl_sync(0xffffffffu, base, 0) + c0;
+      const unsigned int b0 = base32 + c0;
       const unsigned int n = min(CL2, total - c0);
       for (unsigned int i = lane; i < n; i += 32) {
         const unsigned int e = sl2[i], c = e >> 8, w = e & 0xFFu;
-        const unsigned long long slot = b0 + i;
-        if (slot < ds) {
+        const unsigned int slot = b0 + i;
+        if (slot < ds32) {
           const unsigned int v1 = sv12[c];
 #pragma unroll
           for (int q = 0; q < W; ++q) {
@@ -943,17 +963,17 @@ __device__ __forceinline__ void process_bitset_fused(const EngineParams& p, cons
   };
 
   const unsigned int pf = p.pf >= 1 && p.pf <= (unsigned)P ? p.pf : (unsigned)P;
-  for (unsigned long long wb = pl.begin + gwarp; wb < pl.end; wb += pf * T) {
-    const unsigned long long t0 = wb + lane;
+  for (unsigned int wb = gwarp; wb < nrec; wb += pf * T) {
+    const unsigned int t0 = wb + lane;
 #pragma unroll
     for (int j = 0; j < P; ++j) {
-      const unsigned long long i = t0 + (unsigned long long)j * T;
-      const bool valid = (unsigned)j < pf && i < pl.end;
+      const unsigned int i = t0 + j * T;
+      const bool valid = (unsigned)j < pf && i < nrec;
       unsigned long long B[W];
 #pragma unroll
-      for (int k = 0; k < W; ++k) B[k] = valid ? ldcg64(sB + k * ss + i) : ~0ull;
-      const unsigned long long H = valid ? ldcg64(sH + i) : 0ull;
-      const unsigned int M = valid ? ldcg32(sM + i) : 0u;
+      for (int k = 0; k < W; ++k) B[k] = valid ? ldcg64(sB0 + k * ss + i) : ~0ull;
+      const unsigned long long H = valid ? ldcg64(sH0 + i) : 0ull;
+      const unsigned int M = valid ? ldcg32(sM0 + i) : 0u;
       const unsigned int v1 = M & 0xFFFFu, vt = M >> 16;
       const unsigned int pj = j * 32 + lane;
 #pragma unroll
@@ -968,14 +988,15 @@ __device__ __forceinline__ void process_bitset_fused(const EngineParams& p, cons
     list_and_work();
   }
   // hist[t+1] and hist[t+2]: two block sums
-  block_sum3_u64(nx, ncyc1, hacc, s_red);
+  unsigned long long nx64 = nx, ncyc1_64 = ncyc1, ncyc2_64 = ncyc2;
+  block_sum3_u64(nx64, ncyc1_64, hacc, s_red);
   __syncthreads();
   unsigned long long z0 = 0, z1 = 0;
-  block_sum3_u64(ncyc2, z0, z1, s_red);
+  block_sum3_u64(ncyc2_64, z0, z1, s_red);
   if (tid == 0) {
-    if (nx) atomicAdd(&p.ctl->nxt[s % 3], nx);
-    if (ncyc1) atomicAdd(&p.hist[t + 1], ncyc1);
-    if (ncyc2) atomicAdd(&p.hist[t + 2], ncyc2);
+    if (nx64) atomicAdd(&p.ctl->nxt[s % 3], nx64);
+    if (ncyc1_64) atomicAdd(&p.hist[t + 1], ncyc1_64);
+    if (ncyc2_64) atomicAdd(&p.hist[t + 2], ncyc2_64);
     if (hacc) atomicAdd(p.hash, hacc);
   }
 }
