@@ -574,3 +574,56 @@ def test_host_frontier_too_small_reports_capacity(cc):
         # the context stays usable
     with cc.Context(frontier_bytes=1 << 30) as c:
         _same(c.enumerate(g), oracle.enumerate_cycles(g))
+
+
+# ------------------------------------------------------------------ edge cases of the newer entry points
+
+def test_host_frontier_with_cycle_lists(cc):
+    # the host frontier moves CSR frames (cycle lists force CSR records); the listed cycles
+    # are the oracle's
+    g = I.grid(7, 7)
+    ref = oracle.enumerate_cycles(g, cycles=True)
+    with cc.Context(frontier_bytes=128 << 10, host_frontier_bytes=1 << 30) as c, c.load(g) as lg:
+        r = lg.enumerate(0, cycles=True)
+        _same(r, ref)
+        assert sorted(r.cycles) == sorted(ref.cycles)
+        assert r.info.host_offloads > 0
+
+
+@pytest.mark.parametrize("L", [3, 4, 5])
+def test_enumerate_part_short_bounds_and_empty_parts(ctx, L):
+    # more parts than triplets: some parts are empty; short length bounds
+    g = I.wheel(5)
+    nparts = 64
+    whole = oracle.enumerate_cycles(g, max_len=L)
+    with ctx.load(g) as lg:
+        tot = np.zeros_like(whole.hist)
+        hsh = 0
+        empty = 0
+        for part in range(nparts):
+            r = lg.enumerate(L, part=part, nparts=nparts)
+            _same(r, oracle.enumerate_cycles(g, max_len=L, part=part, nparts=nparts))
+            tot += r.hist
+            hsh = (hsh + r.hash) % 2 ** 64
+            empty += r.total == 0
+        assert tot.tolist() == whole.hist.tolist() and hsh == whole.hash and empty > 0
+
+
+def test_batch_degenerate_graphs(cc, ctx):
+    # graphs without cycles, without edges, with fewer than 3 vertices, and length bounds 3
+    graphs = [I.empty(1), I.empty(2), I.path(2), I.empty(5), I.path(7), I.random_tree(20, 3), I.cycle(3),
+              I.complete(4), I.grid(3, 3)]
+    for L in (0, 3, 4):
+        hist, hsh, paths, done, info = ctx.batch(graphs, max_len=L)
+        _check_batch(graphs, _oracle_many(graphs, L), hist, hsh, paths)
+
+
+def test_niche_overlap_small_webs(cc, ctx):
+    for n, lists in [(1, [[0]]), (2, [[], []]), (2, [[0], [0]]), (3, [[0], [0], [0]]), (4, [[], [], [], []])]:
+        ptr = np.zeros(n + 1, dtype=np.uint32)
+        ptr[1:] = np.cumsum([len(x) for x in lists])
+        idx = np.array([z for x in lists for z in x], dtype=np.uint32)
+        s, rp, col = cc.cc_niche_overlap(ctx.handle, n, ptr, idx)
+        assert s == cc.CC_OK
+        ref_rp, ref_col = oracle.niche_overlap(n, ptr, idx)
+        assert rp.tolist() == ref_rp.tolist() and col.tolist() == ref_col.tolist()
