@@ -1003,9 +1003,12 @@ __device__ __forceinline__ void process_bitset_fused(const EngineParams& p, cons
 
 // The batch form of the flattened expansion (records of many graphs in one frontier; M
 // holds v1, vt, t and the graph's slot g, whose rows and r-table sit at g * 64).  Per-path
-// statistics (paths expanded, children and closings per (slot, length)) are accumulated
-// in lane order as runs of one key, as in the per-lane form; closing hashes are summed per
-// lane while the slot stays the same and added to its sum when it changes.
+// statistics (paths expanded, children, closings and their hashes per (slot, length)) are
+// accumulated in lane order as runs of one key, as in the per-lane form.  A path closes
+// few cycles (about one for every five paths stored), so each lane hashes its own paths'
+// closings in place.  The children are worked off one per lane: child i of a round belongs
+// to the last lane whose first child index is at most i (a binary search over the lanes'
+// exclusive prefix counts, by shuffles), and is the k-th set bit of that lane's masks.
 //
 // Work distribution: a warp takes contiguous chunks of the step's records from a step
 // counter (one atomic per chunk), so its rounds mostly stay inside one graph's run of
@@ -1019,18 +1022,19 @@ template <int NT>
 __device__ __forceinline__ void process_multi_flat(const EngineParams& p, const StepPlan& pl,
                                                    const unsigned long long* adj, const unsigned long long* rtab) {
   constexpr int P = KindTraits<Kind::Multi>::P;
-  constexpr unsigned int CL = FlatSmem<1, P, NT>::CL;
-  __shared__ FlatSmem<1, P, NT> fs;
+  static_assert(P == 2, "the batch form takes two paths per lane and round");
+  __shared__ unsigned long long s_nb[NT / 32][P * 32];  // B | Adj(vt) per staged path
+  __shared__ unsigned long long s_h[NT / 32][P * 32];   // H per staged path
+  __shared__ unsigned int s_meta[NT / 32][P * 32];
   __shared__ unsigned long long s_gadj[NT / 32][64];
   __shared__ unsigned long long s_grt[NT / 32][64];
   __shared__ unsigned long long s_rb[NT / 32][2][P * 32];  // records of this round and the next
   __shared__ unsigned long long s_rh[NT / 32][2][P * 32];
   __shared__ unsigned int s_rm[NT / 32][2][P * 32];
   const unsigned int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  unsigned long long* snb = fs.nb[wid];
-  unsigned long long* sh = fs.h[wid];
-  unsigned int* smeta = fs.v1[wid];  // v1 | t << 6 | g << 12 | (t + 2 < L'_g) << 31
-  unsigned int* sl = fs.list[wid];
+  unsigned long long* snb = s_nb[wid];
+  unsigned long long* sh = s_h[wid];
+  unsigned int* smeta = s_meta[wid];  // v1 | t << 6 | g << 12 | (t + 2 < L'_g) << 31
   unsigned long long* ga = s_gadj[wid];
   unsigned long long* gr = s_grt[wid];
   const unsigned long long ss = pl.src_stride, ds = pl.dst_stride;
@@ -1050,13 +1054,6 @@ __device__ __forceinline__ void process_multi_flat(const EngineParams& p, const 
   unsigned int nx = 0;  // children of this lane's stored children (fits 32 bits per lane and step)
   StatRun run;
   run.key = 0xFFFFFFFFu;
-  unsigned long long hacc = 0;      // closing hashes of slot hkey, per lane
-  unsigned int hkey = 0xFFFFFFFFu;
-  auto flush_hash = [&]() {
-    const unsigned long long sum = warp_sum_u64(hacc);
-    if (lane == 0 && hkey != 0xFFFFFFFFu && sum) atomicAdd(&p.hash[hkey], sum);
-    hacc = 0;
-  };
   unsigned int cg = 0xFFFFFFFFu;  // graph staged in ga / gr
   unsigned int cL = 0;            // its L'
   auto A = [&](unsigned int g, unsigned int v) -> unsigned long long {
@@ -1066,87 +1063,64 @@ __device__ __forceinline__ void process_multi_flat(const EngineParams& p, const 
     return g == cg ? gr[v] : __ldg(rtab + (unsigned long long)g * 64ull + v);
   };
 
-  // children entries [0, n) take slots base + [0, n)
-  auto flush_children = [&](unsigned int n, unsigned int base) {
-    __syncwarp();
-    for (unsigned int i = lane; i < n; i += 32) {
-      const unsigned int e = sl[i], pj = e >> 8, v = e & 0xFFu;
-      const unsigned int meta = smeta[pj], v1 = meta & 63u, tt = (meta >> 6) & 63u, g = (meta >> 12) & 0x7FFFFu;
-      const unsigned int slot = base + i;
-      if (slot < ds32) {
-        const unsigned long long nb = snb[pj];
-        dB[slot] = nb;
-        dH[slot] = sh[pj] + R(g, v);
-        dM[slot] = v1 | (v << 6) | ((tt + 1) << 12) | (g << 18);
-        const unsigned int nc = (meta >> 31) ? __popcll(A(g, v) & ~nb & ~A(g, v1)) : 0u;
-        dN[slot] = (unsigned char)nc;
-        nx += nc;
-      } else {
-        set_err(p.ctl, kDevBounds, 1);
-      }
-    }
-    __syncwarp();
-  };
-  auto flush_closings = [&](unsigned int n) {
-    __syncwarp();
-    for (unsigned int r0 = 0; r0 < n; r0 += 32) {
-      const unsigned int i = r0 + lane;
-      unsigned int g = 0xFFFFFFFFu;
-      unsigned long long h = 0;
-      if (i < n) {
-        const unsigned int e = sl[i], pj = e >> 8, v = e & 0xFFu;
-        const unsigned int meta = smeta[pj], tt = (meta >> 6) & 63u;
-        g = (meta >> 12) & 0x7FFFFu;
-        h = mix64(sh[pj] + R(g, v) + (unsigned long long)(tt + 1) * kGamma);
-      }
-      // usually every active lane of a round closes cycles of one slot: summed per lane
-      // until the slot changes; otherwise one atomic per lane
-      const unsigned int g0 = __shfl_sync(0xffffffffu, g, 0);  // lane 0 is active (n > r0)
-      if (__all_sync(0xffffffffu, g == g0 || i >= n)) {
-        if (g0 != hkey) {
-          flush_hash();
-          hkey = g0;
-        }
-        hacc += h;
-      } else if (i < n) {
-        atomicAdd(&p.hash[g], h);
-      }
-    }
-    __syncwarp();
-  };
   unsigned long long m[P];
   unsigned int cnext = 0, cend_slot = 0;  // the chunk's reserved child slots (warp-uniform)
-  auto list_and_work = [&](bool children) {
-    unsigned int cnt = 0;
-#pragma unroll
-    for (int j = 0; j < P; ++j) cnt += __popcll(m[j]);
+  // The round's children <p, v> (masks m[0], m[1] of each lane's two paths) take the next
+  // slots of the chunk's range, in lane order.
+  auto children = [&]() {
+    const unsigned int c0n = __popcll(m[0]);
+    const unsigned int cnt = c0n + __popcll(m[1]);
     unsigned int incl = cnt;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
       const unsigned int y = __shfl_up_sync(0xffffffffu, incl, o);
       if (lane >= (unsigned)o) incl += y;
     }
-    const unsigned int excl = incl - cnt, total = __shfl_sync(0xffffffffu, incl, 31);
-    // a round's children take the next slots of the chunk's reserved range
+    const unsigned int excl = incl - cnt, n = __shfl_sync(0xffffffffu, incl, 31);
     const unsigned int base = cnext;
-    if (children) cnext += total;
-    for (unsigned int c0 = 0; c0 < total; c0 += CL) {
-      if (cnt && excl < c0 + CL && excl + cnt > c0) {
-        unsigned int idx = excl;
+    cnext += n;
+    __syncwarp();  // the staged paths (snb, sh, smeta) of every lane
+    for (unsigned int w0 = 0; w0 < n; w0 += 32) {
+      const unsigned int i = w0 + lane;
+      // owner: the last lane whose first child index is at most i (a lane without children
+      // shares its index with the next lane, so the last such lane has child i)
+      unsigned int o = 0, eo = 0;
 #pragma unroll
-        for (int j = 0; j < P; ++j) {
-          unsigned long long b = m[j];
-          while (b) {
-            const unsigned int v = __ffsll((long long)b) - 1;
-            b &= b - 1;
-            if (idx >= c0 && idx < c0 + CL) sl[idx - c0] = (unsigned int)(j * 32 + lane) << 8 | v;
-            ++idx;
-          }
+      for (unsigned int st = 16; st >= 1; st >>= 1) {
+        const unsigned int e = __shfl_sync(0xffffffffu, excl, o + st);
+        if (e <= i) {
+          o += st;
+          eo = e;
         }
       }
-      if (children) flush_children(min(CL, total - c0), base + c0);
-      else flush_closings(min(CL, total - c0));
+      const unsigned long long b0 = __shfl_sync(0xffffffffu, m[0], o), b1 = __shfl_sync(0xffffffffu, m[1], o);
+      const unsigned int c0o = __shfl_sync(0xffffffffu, c0n, o);
+      if (i < n) {
+        unsigned int k = i - eo, j = 0;
+        unsigned long long b = b0;
+        if (k >= c0o) {
+          k -= c0o;
+          j = 1;
+          b = b1;
+        }
+        for (; k; --k) b &= b - 1;  // the k-th set bit of the path's child mask
+        const unsigned int v = __ffsll((long long)b) - 1, pj = j * 32u + o;
+        const unsigned int meta = smeta[pj], v1 = meta & 63u, tt = (meta >> 6) & 63u, g = (meta >> 12) & 0x7FFFFu;
+        const unsigned int slot = base + i;
+        if (slot < ds32) {
+          const unsigned long long nb = snb[pj];
+          dB[slot] = nb;
+          dH[slot] = sh[pj] + R(g, v);
+          dM[slot] = v1 | (v << 6) | ((tt + 1) << 12) | (g << 18);
+          const unsigned int nc = (meta >> 31) ? __popcll(A(g, v) & ~nb & ~A(g, v1)) : 0u;
+          dN[slot] = (unsigned char)nc;
+          nx += nc;
+        } else {
+          set_err(p.ctl, kDevBounds, 1);
+        }
+      }
     }
+    __syncwarp();
   };
 
   const unsigned int pf = p.pf >= 1 && p.pf <= (unsigned)P ? p.pf : (unsigned)P;
@@ -1234,19 +1208,44 @@ __device__ __forceinline__ void process_multi_flat(const EngineParams& p, const 
         nc[j] = __popcll(m[j]);
         nk[j] = __popcll(ch[j]);
       }
-      // per (slot, length) counts, as runs of one key (no hash here: closings add theirs)
+      // the closings <p, v>, hashed in place: h(C) = mix(H + r(v) + (t+1) gamma), one bit
+      // of either path's mask per iteration
+      static_assert(P == 2, "the closing loop takes two paths per lane");
+      unsigned long long hs0 = 0, hs1 = 0;
+      {
+        unsigned long long b0 = m[0], b1 = m[1];
+        if (b0 | b1) {
+          const unsigned long long hb0 = sh[lane] + (unsigned long long)((key[0] & 63u) + 1u) * kGamma;
+          const unsigned long long hb1 = sh[32 + lane] + (unsigned long long)((key[1] & 63u) + 1u) * kGamma;
+          do {
+            const bool f = b0 != 0;
+            const unsigned long long b = f ? b0 : b1;
+            const unsigned int v = __ffsll((long long)b) - 1;
+            const unsigned long long h = mix64((f ? hb0 : hb1) + R((f ? key[0] : key[1]) >> 6, v));
+            if (f) {
+              hs0 += h;
+              b0 &= b0 - 1;
+            } else {
+              hs1 += h;
+              b1 &= b1 - 1;
+            }
+          } while (b0 | b1);
+        }
+      }
+      // per (slot, length) counts and closing hashes, as runs of one key
 #pragma unroll
       for (int j = 0; j < P; ++j) {
         const unsigned int k = key[j];
+        const unsigned long long hj = j == 0 ? hs0 : hs1;
         const bool v = k != 0xFFFFFFFFu;
         const bool m0 = v && k == run.key;
-        if (m0) run.add(nc[j], nk[j], 0ull);
+        if (m0) run.add(nc[j], nk[j], hj);
         const unsigned int rest = __ballot_sync(0xffffffffu, v && !m0);
         if (rest) {
           run.flush(p, s);
           run.key = __shfl_sync(0xffffffffu, k, 31 - __clz(rest));
           const bool m1 = v && !m0 && k == run.key;
-          if (m1) run.add(nc[j], nk[j], 0ull);
+          if (m1) run.add(nc[j], nk[j], hj);
           unsigned int pending = __ballot_sync(0xffffffffu, v && !m0 && !m1);
           while (pending) {
             const int leader = __ffs(pending) - 1;
@@ -1255,24 +1254,22 @@ __device__ __forceinline__ void process_multi_flat(const EngineParams& p, const 
             const unsigned int grp = __ballot_sync(0xffffffffu, mine);
             StatRun one;
             one.key = lk;
-            if (mine) one.add(nc[j], nk[j], 0ull);
+            if (mine) one.add(nc[j], nk[j], hj);
             one.flush(p, s);
             pending &= ~grp;
           }
         }
       }
-      list_and_work(false);
       if (store) {
 #pragma unroll
         for (int j = 0; j < P; ++j) m[j] = ch[j];
-        list_and_work(true);
+        children();
       }
     }
     // (the children listed equal the child counts the records carry; a mismatch would be a
     // bug, reported instead of writing into another chunk's slots)
     if (store && cnext != cend_slot && lane == 0) set_err(p.ctl, kDevBounds, 6);
   }
-  flush_hash();
   run.flush(p, s);
   const unsigned long long tot = warp_sum_u64((unsigned long long)nx);
   if (lane == 0 && tot) atomicAdd(&p.ctl->nxt[s % 3], tot);

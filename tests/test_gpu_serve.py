@@ -83,8 +83,12 @@ def test_serve_length_bound_and_small_budget(cc):
 
 
 def test_serve_spills_when_frontier_is_small(cc):
+    # grid 8x8 alone peaks at about 115 MB of frontier, so 64 MiB spills.  Paths of up to 64
+    # vertices in flight give each stored level an equal share of the free arena (about
+    # 1700 paths per step here; 24 MiB took close to 200,000 rounds, a count that varies
+    # from run to run with the order in which warps write the records).
     graphs = [I.grid(8, 8), I.gnp(40, 0.2, 1), I.grid(7, 7)] + _requests(20, 5)
-    with cc.Context(frontier_bytes=24 << 20) as ctx:
+    with cc.Context(frontier_bytes=64 << 20) as ctx:
         ids, results, overlap, busy = _serve(cc, ctx, graphs, waves=3, slots=32, reserve_paths=1 << 12)
         ref_ctx = cc.Context(frontier_bytes=2 << 30)
         for rid, g in ids.items():
