@@ -203,14 +203,21 @@ def _frontier_bytes(args, default_mb):
 
 # ------------------------------------------------------------------ committed ncu summaries
 
-def _engine_fingerprint() -> str:
-    """Hash of the engine's code (cc_engine.cu + cc_internal.cuh without comments and
-    whitespace), so that a committed ncu capture is used only for the code it measured."""
+_FORM_SOURCES = {"Multi": "cc_expand_multi.cuh", "Bitset": "cc_expand_bitset.cuh", "Csr": "cc_expand_csr.cuh"}
+
+
+def _engine_fingerprint(kernel: str) -> str:
+    """Hash of the code a kernel runs, without comments and whitespace: the persistent
+    kernel and planner (cc_engine.cu), the shared helpers (cc_internal.cuh) and the
+    expansion form of its record kind (cc_expand_<form>.cuh), so that a committed ncu
+    capture is used only for the code it measured, and a change to one form leaves the
+    other forms' captures valid."""
     import hashlib
     import re
     csrc = os.path.join(ROOT, "paper_1410_4876_gb300", "csrc")
+    forms = [v for k, v in _FORM_SOURCES.items() if k in kernel] or sorted(_FORM_SOURCES.values())
     text = ""
-    for f in ("cc_engine.cu", "cc_internal.cuh"):
+    for f in ["cc_engine.cu", "cc_internal.cuh"] + forms:
         src = open(os.path.join(csrc, f)).read()
         src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
         src = re.sub(r"//[^\n]*", "", src)
@@ -226,7 +233,7 @@ def _profile(name: str) -> dict:
         d = json.load(open(os.path.join(ROOT, "profiles", name + ".json")))
     except Exception:
         return {}
-    if d.get("source_fingerprint") != _engine_fingerprint():
+    if d.get("source_fingerprint") != _engine_fingerprint(d.get("kernel", "")):
         d.pop("dram_bytes_per_path", None)
     return d
 

@@ -344,6 +344,31 @@ __device__ __forceinline__ unsigned int block_exclusive_scan(unsigned int v, uns
   return before + x - v;
 }
 
+// Entry i of a warp's list of set bits, the lanes' bits in lane order (`excl` = this lane's
+// exclusive prefix count of its bits): its owner is the last lane whose first entry is at
+// most i (a lane without bits shares its prefix with the next lane, so for i below the
+// total the last such lane has entry i).  Binary search over the lanes by shuffles; every
+// lane of the warp calls it.  `rank` receives i's rank among the owner's bits.
+__device__ __forceinline__ unsigned int list_owner(unsigned int excl, unsigned int i, unsigned int& rank) {
+  unsigned int o = 0, eo = 0;
+#pragma unroll
+  for (unsigned int st = 16; st >= 1; st >>= 1) {
+    const unsigned int e = __shfl_sync(0xffffffffu, excl, o + st);
+    if (e <= i) {
+      o += st;
+      eo = e;
+    }
+  }
+  rank = i - eo;
+  return o;
+}
+
+// Index of the r-th set bit of b (r < popc(b)).
+__device__ __forceinline__ unsigned int nth_set_bit(unsigned long long b, unsigned int r) {
+  for (; r; --r) b &= b - 1;
+  return __ffsll((long long)b) - 1;
+}
+
 __device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
