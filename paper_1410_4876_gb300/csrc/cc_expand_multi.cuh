@@ -51,9 +51,10 @@ struct StatRun {
 // records while the chunks balance the load between warps.  Each record carries its exact
 // child count (N, written with it), so the warp reserves the child slots of a whole chunk
 // with one atomic before expanding it: a single counter taking one atomic per round was
-// the hot spot of the whole grid.  The rows, r-table and L' of the graph a warp is working
-// on are staged in the warp's shared memory when the graph changes; records of any other
-// graph in the same round read them from global memory.
+// the hot spot of the whole grid.  The rows, r-table and L' of a record's graph (1 KB per
+// graph) are read through the L1 cache at (slot << 6 | v): a copy staged in the warp's
+// shared memory, with a branch for records of another graph, cost more instructions than
+// the L1 hits it saved.
 template <int NT>
 __device__ __forceinline__ void process_multi_flat(const EngineParams& p, const StepPlan& pl,
                                                    const unsigned long long* adj, const unsigned long long* rtab) {
@@ -62,8 +63,6 @@ __device__ __forceinline__ void process_multi_flat(const EngineParams& p, const 
   __shared__ unsigned long long s_nb[NT / 32][P * 32];  // B | Adj(vt) per staged path
   __shared__ unsigned long long s_h[NT / 32][P * 32];   // H per staged path
   __shared__ unsigned int s_meta[NT / 32][P * 32];
-  __shared__ unsigned long long s_gadj[NT / 32][64];
-  __shared__ unsigned long long s_grt[NT / 32][64];
   __shared__ unsigned long long s_rb[NT / 32][2][P * 32];  // records of this round and the next
   __shared__ unsigned long long s_rh[NT / 32][2][P * 32];
   __shared__ unsigned int s_rm[NT / 32][2][P * 32];
@@ -71,8 +70,6 @@ __device__ __forceinline__ void process_multi_flat(const EngineParams& p, const 
   unsigned long long* snb = s_nb[wid];
   unsigned long long* sh = s_h[wid];
   unsigned int* smeta = s_meta[wid];  // v1 | t << 6 | g << 12 | (t + 2 < L'_g) << 31
-  unsigned long long* ga = s_gadj[wid];
-  unsigned long long* gr = s_grt[wid];
   const unsigned long long ss = pl.src_stride, ds = pl.dst_stride;
   const unsigned long long* sB = reinterpret_cast<const unsigned long long*>(p.arena + pl.src_base);
   const unsigned long long* sH = sB + ss;
@@ -90,13 +87,11 @@ __device__ __forceinline__ void process_multi_flat(const EngineParams& p, const 
   unsigned int nx = 0;  // children of this lane's stored children (fits 32 bits per lane and step)
   StatRun run;
   run.key = 0xFFFFFFFFu;
-  unsigned int cg = 0xFFFFFFFFu;  // graph staged in ga / gr
-  unsigned int cL = 0;            // its L'
   auto A = [&](unsigned int g, unsigned int v) -> unsigned long long {
-    return g == cg ? ga[v] : __ldg(adj + (unsigned long long)g * 64ull + v);
+    return __ldg(adj + ((g << 6) | v));
   };
   auto R = [&](unsigned int g, unsigned int v) -> unsigned long long {
-    return g == cg ? gr[v] : __ldg(rtab + (unsigned long long)g * 64ull + v);
+    return __ldg(rtab + ((g << 6) | v));
   };
 
   unsigned long long m[P] = {};
@@ -198,18 +193,6 @@ __device__ __forceinline__ void process_multi_flat(const EngineParams& p, const 
       if (wb + RW < cend) prefetch(wb + RW, buf ^ 1u);
       else cp_async_commit();  // (an empty group: the wait below still means "this round")
       cp_async_wait_1();
-      // the graph of the round's first record (always valid): stage it if it changed
-      const unsigned int g0 = __shfl_sync(0xffffffffu, s_rm[wid][buf][lane], 0) >> 18;
-      if (g0 != cg) {
-        __syncwarp();
-        ga[lane] = __ldg(adj + (unsigned long long)g0 * 64ull + lane);
-        ga[lane + 32] = __ldg(adj + (unsigned long long)g0 * 64ull + lane + 32);
-        gr[lane] = __ldg(rtab + (unsigned long long)g0 * 64ull + lane);
-        gr[lane + 32] = __ldg(rtab + (unsigned long long)g0 * 64ull + lane + 32);
-        cL = p.Lg[g0];
-        cg = g0;
-        __syncwarp();
-      }
       const unsigned int t0 = wb + lane;
       unsigned long long ch[P];
       unsigned int key[P], nc[P], nk[P];
@@ -221,7 +204,7 @@ __device__ __forceinline__ void process_multi_flat(const EngineParams& p, const 
         const unsigned long long H = valid ? s_rh[wid][buf][j * 32 + lane] : 0ull;
         const unsigned int M = valid ? s_rm[wid][buf][j * 32 + lane] : 0u;
         const unsigned int v1 = M & 63u, vt = (M >> 6) & 63u, tt = (M >> 12) & 63u, g = M >> 18;
-        const unsigned int Lr = valid ? (g == cg ? cL : p.Lg[g]) : 0u;
+        const unsigned int Lr = valid ? __ldg(p.Lg + g) : 0u;
         const unsigned long long at = A(g, vt), a1 = A(g, v1);
         const unsigned long long cand = at & ~B;
         m[j] = (tt + 1 <= Lr) ? (cand & a1) : 0ull;
