@@ -337,7 +337,10 @@ __global__ void __launch_bounds__(NT, NT >= 1024 ? 1 : KindTraits<K>::minB) engi
   const unsigned int* nrow = p.nrow;
   const unsigned short* ncol = p.ncol;
   const unsigned long long* nsig = p.nsig;
-  if (p.smem_graph) {
+  // one graph's bitset rows (n <= 256: at most 10 KB with the r-table) are always staged,
+  // so the expansion's row reads are known to be shared-memory loads
+  constexpr bool kStageAlways = !KindTraits<K>::csr && !KindTraits<K>::multi;
+  if (kStageAlways || p.smem_graph) {
     // stage the relabelled graph into shared memory with the bulk-copy (TMA) engine:
     // bitset rows + r-table, or CSR rows + neighbours + neighbour signatures
     if (tid == 0) mbar_init(&s_mbar, 1);
