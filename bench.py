@@ -24,6 +24,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import subprocess
 import sys
@@ -102,6 +103,17 @@ def max_over_ranks(value: float, dist, device=None) -> float:
     t = torch.tensor([float(value)], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def steps_for_clocks(steps: int, ms_per_step: float, dist=None, device=None, region_ms: float = 1500.0,
+                     cap: int = 5000) -> int:
+    """Timed steps for a short workload: at least `steps`, and enough to span about
+    `region_ms` so that the 200 ms clock sampler sees the GPU under load several times
+    (the same count on every rank)."""
+    k = steps
+    if ms_per_step > 0:
+        k = max(steps, min(cap, int(math.ceil(region_ms / ms_per_step))))
+    return int(max_over_ranks(k, dist, device))
 
 
 def sum_results(hist, hsh: int, dist, device=None):
@@ -434,6 +446,11 @@ def single_leg(args, cc, work, steps, warmup, stream, flush, dev, dist, profile,
     for _ in range(warmup):
         step()
     torch.cuda.synchronize()
+    # a step takes about a millisecond: time enough of them for the clock record
+    t0 = time.perf_counter()
+    step()
+    torch.cuda.synchronize()
+    steps = steps_for_clocks(steps, (time.perf_counter() - t0) * 1000.0, dist, dev)
     ev = _events(torch, steps)
     cycles = paths = 0
     eng_ms, alg, launches = 0.0, 0, 0

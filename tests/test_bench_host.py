@@ -84,3 +84,12 @@ def test_reference_arm_other_ranks_exit_quietly():
     # under torchrun only rank 0 runs the reference arm; the others exit 0 without output
     env = {"RANK": "1", "WORLD_SIZE": "2", "LOCAL_RANK": "1", "MASTER_ADDR": "127.0.0.1", "MASTER_PORT": "29561"}
     assert _run_bench(["--impl", "reference", "--workload", "grid6", "--steps", "1", "--warmup", "1"], env) == []
+
+
+def test_steps_for_clocks_spans_the_sampler():
+    b = _bench()
+    # a 0.9 ms step needs about 1667 steps for a 1.5 s region; long steps keep the count
+    assert b.steps_for_clocks(10, 0.9) == 1667
+    assert b.steps_for_clocks(20, 120.0) == 20
+    assert b.steps_for_clocks(10, 1e-4) == 5000   # capped
+    assert b.steps_for_clocks(7, 0.0) == 7         # no estimate: as asked
