@@ -88,7 +88,7 @@ struct KindTraits {
   // warp per round)
   static constexpr int PF = K == Kind::Bitset1 ? 3 : (K == Kind::Bitset2 ? 2 : 1);
   // children staged per batch in a two-level step, in rounds of 32 (shared memory bound)
-  static constexpr int PF2 = K == Kind::Bitset1 ? 2 : 1;
+  static constexpr int PF2 = K == Kind::Bitset1 ? 4 : 1;
 };
 
 template <Kind K>
