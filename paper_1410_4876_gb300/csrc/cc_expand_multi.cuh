@@ -62,14 +62,16 @@ __device__ __forceinline__ void process_multi_flat(const EngineParams& p, const 
   static_assert(P == 2, "the batch form takes two paths per lane and round");
   __shared__ unsigned long long s_nb[NT / 32][P * 32];  // B | Adj(vt) per staged path
   __shared__ unsigned long long s_h[NT / 32][P * 32];   // H per staged path
-  __shared__ unsigned int s_meta[NT / 32][P * 32];
+  __shared__ unsigned long long s_x[NT / 32][P * 32];   // B | Adj(vt) | Adj(v1), or ~0 at t + 2 = L'
+  __shared__ unsigned int s_mb[NT / 32][P * 32];        // a child's M without its v_t
   __shared__ unsigned long long s_rb[NT / 32][2][P * 32];  // records of this round and the next
   __shared__ unsigned long long s_rh[NT / 32][2][P * 32];
   __shared__ unsigned int s_rm[NT / 32][2][P * 32];
   const unsigned int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   unsigned long long* snb = s_nb[wid];
   unsigned long long* sh = s_h[wid];
-  unsigned int* smeta = s_meta[wid];  // v1 | t << 6 | g << 12 | (t + 2 < L'_g) << 31
+  unsigned long long* sx = s_x[wid];
+  unsigned int* smb = s_mb[wid];  // v1 | (t + 1) << 12 | g << 18
   const unsigned long long ss = pl.src_stride, ds = pl.dst_stride;
   const unsigned long long* sB = reinterpret_cast<const unsigned long long*>(p.arena + pl.src_base);
   const unsigned long long* sH = sB + ss;
@@ -110,7 +112,7 @@ __device__ __forceinline__ void process_multi_flat(const EngineParams& p, const 
     const unsigned int excl = incl - cnt, n = __shfl_sync(0xffffffffu, incl, 31);
     const unsigned int base = cnext;
     cnext += n;
-    __syncwarp();  // the staged paths (snb, sh, smeta) of every lane
+    __syncwarp();  // the staged paths (snb, sh, sx, smb) of every lane
     for (unsigned int w0 = 0; w0 < n; w0 += 32) {
       const unsigned int i = w0 + lane;
       unsigned int k;
@@ -126,14 +128,15 @@ __device__ __forceinline__ void process_multi_flat(const EngineParams& p, const 
           b = b1;
         }
         const unsigned int v = nth_set_bit(b, k), pj = j * 32u + o;
-        const unsigned int meta = smeta[pj], v1 = meta & 63u, tt = (meta >> 6) & 63u, g = (meta >> 12) & 0x7FFFFu;
+        const unsigned int mb = smb[pj], g = mb >> 18;
         const unsigned int slot = base + i;
         if (slot < ds32) {
           const unsigned long long nb = snb[pj];
           dB[slot] = nb;
           dH[slot] = sh[pj] + R(g, v);
-          dM[slot] = v1 | (v << 6) | ((tt + 1) << 12) | (g << 18);
-          const unsigned int nc = (meta >> 31) ? __popcll(A(g, v) & ~nb & ~A(g, v1)) : 0u;
+          dM[slot] = mb | (v << 6);
+          // the child's own children: Adj(v) minus its blocked set and Adj(v1)
+          const unsigned int nc = __popcll(A(g, v) & ~sx[pj]);
           dN[slot] = (unsigned char)nc;
           nx += nc;
         } else {
@@ -212,7 +215,8 @@ __device__ __forceinline__ void process_multi_flat(const EngineParams& p, const 
         const unsigned int pj = j * 32 + lane;
         snb[pj] = B | at;
         sh[pj] = H;
-        smeta[pj] = v1 | (tt << 6) | (g << 12) | ((tt + 2 < Lr) ? 0x80000000u : 0u);
+        sx[pj] = (tt + 2 < Lr) ? (B | at | a1) : ~0ull;
+        smb[pj] = v1 | ((tt + 1) << 12) | (g << 18);
         key[j] = valid ? (g << 6 | tt) : 0xFFFFFFFFu;
         nc[j] = __popcll(m[j]);
         nk[j] = __popcll(ch[j]);
