@@ -321,7 +321,10 @@ __device__ __forceinline__ void cluster_barrier() {
 // hardware cluster barrier; it runs while the frames are small (p.handover) and leaves
 // the state for the grid launch that follows.  Every CTA computes the same plan, so all
 // CTAs of the cluster execute the same sequence of cluster barriers.
-template <Kind K, int NT>
+// SG: the graph is staged in shared memory (known at compile time, so the expansion's graph
+// reads are shared-memory loads): always for one graph's bitset rows (n <= 256: at most 10 KB
+// with the r-table), never for the batch, and for CSR graphs whose rows fit.
+template <Kind K, int NT, bool SG>
 __global__ void __launch_bounds__(NT, NT >= 1024 ? 1 : KindTraits<K>::minB) engine_kernel(EngineParams p) {
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ StepPlan pl;
@@ -337,10 +340,7 @@ __global__ void __launch_bounds__(NT, NT >= 1024 ? 1 : KindTraits<K>::minB) engi
   const unsigned int* nrow = p.nrow;
   const unsigned short* ncol = p.ncol;
   const unsigned long long* nsig = p.nsig;
-  // one graph's bitset rows (n <= 256: at most 10 KB with the r-table) are always staged,
-  // so the expansion's row reads are known to be shared-memory loads
-  constexpr bool kStageAlways = !KindTraits<K>::csr && !KindTraits<K>::multi;
-  if (kStageAlways || p.smem_graph) {
+  if constexpr (SG) {
     // stage the relabelled graph into shared memory with the bulk-copy (TMA) engine:
     // bitset rows + r-table, or CSR rows + neighbours + neighbour signatures
     if (tid == 0) mbar_init(&s_mbar, 1);
@@ -510,24 +510,32 @@ __global__ void __launch_bounds__(NT, NT >= 1024 ? 1 : KindTraits<K>::minB) engi
 
 // ------------------------------------------------------------------ host-side launch helpers
 
-static const void* engine_fn(Kind k) {
+// `staged`: the launch stages the graph in shared memory (p.smem_graph; a CSR graph whose
+// rows fit); one graph's bitset rows always are, the batch's never.
+static const void* engine_fn(Kind k, bool staged) {
   switch (k) {
-    case Kind::Bitset1: return (const void*)engine_kernel<Kind::Bitset1, kMaxThreads>;
-    case Kind::Bitset2: return (const void*)engine_kernel<Kind::Bitset2, kMaxThreads>;
-    case Kind::Bitset4: return (const void*)engine_kernel<Kind::Bitset4, kMaxThreads>;
-    case Kind::Multi: return (const void*)engine_kernel<Kind::Multi, kMaxThreads>;
-    case Kind::Csr: return (const void*)engine_kernel<Kind::Csr, kMaxThreads>;
-    case Kind::Csr16: return (const void*)engine_kernel<Kind::Csr16, kMaxThreads>;
-    case Kind::Csr32: return (const void*)engine_kernel<Kind::Csr32, kMaxThreads>;
+    case Kind::Bitset1: return (const void*)engine_kernel<Kind::Bitset1, kMaxThreads, true>;
+    case Kind::Bitset2: return (const void*)engine_kernel<Kind::Bitset2, kMaxThreads, true>;
+    case Kind::Bitset4: return (const void*)engine_kernel<Kind::Bitset4, kMaxThreads, true>;
+    case Kind::Multi: return (const void*)engine_kernel<Kind::Multi, kMaxThreads, false>;
+    case Kind::Csr:
+      return staged ? (const void*)engine_kernel<Kind::Csr, kMaxThreads, true>
+                    : (const void*)engine_kernel<Kind::Csr, kMaxThreads, false>;
+    case Kind::Csr16:
+      return staged ? (const void*)engine_kernel<Kind::Csr16, kMaxThreads, true>
+                    : (const void*)engine_kernel<Kind::Csr16, kMaxThreads, false>;
+    case Kind::Csr32:
+      return staged ? (const void*)engine_kernel<Kind::Csr32, kMaxThreads, true>
+                    : (const void*)engine_kernel<Kind::Csr32, kMaxThreads, false>;
   }
   return nullptr;
 }
 
 static const void* small_engine_fn(Kind k) {
   switch (k) {
-    case Kind::Bitset1: return (const void*)engine_kernel<Kind::Bitset1, kSmallThreads>;
-    case Kind::Bitset2: return (const void*)engine_kernel<Kind::Bitset2, kSmallThreads>;
-    case Kind::Bitset4: return (const void*)engine_kernel<Kind::Bitset4, kSmallThreads>;
+    case Kind::Bitset1: return (const void*)engine_kernel<Kind::Bitset1, kSmallThreads, true>;
+    case Kind::Bitset2: return (const void*)engine_kernel<Kind::Bitset2, kSmallThreads, true>;
+    case Kind::Bitset4: return (const void*)engine_kernel<Kind::Bitset4, kSmallThreads, true>;
     default: return nullptr;
   }
 }
@@ -554,14 +562,14 @@ static cudaError_t allow_smem(const void* fn, size_t smem) {
 }
 
 cudaError_t engine_occupancy(Kind kind, int block, size_t smem, int* blocks_per_sm) {
-  const void* fn = engine_fn(kind);
+  const void* fn = engine_fn(kind, smem > 0);
   cudaError_t e = allow_smem(fn, smem);
   if (e != cudaSuccess) return e;
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fn, block, smem);
 }
 
 cudaError_t launch_engine(Kind kind, const EngineParams& p, int grid, int block, size_t smem, cudaStream_t st) {
-  const void* fn = engine_fn(kind);
+  const void* fn = engine_fn(kind, p.smem_graph != 0);
   cudaError_t e = allow_smem(fn, smem);
   if (e != cudaSuccess) return e;
   EngineParams copy = p;
