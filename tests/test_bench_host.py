@@ -93,3 +93,25 @@ def test_steps_for_clocks_spans_the_sampler():
     assert b.steps_for_clocks(20, 120.0) == 20
     assert b.steps_for_clocks(10, 1e-4) == 5000   # capped
     assert b.steps_for_clocks(7, 0.0) == 7         # no estimate: as asked
+
+
+def test_engine_fingerprint_is_per_form(tmp_path, monkeypatch):
+    # a capture stays valid while the code its kernel runs is unchanged: editing one
+    # expansion form changes that form's fingerprint only
+    import shutil
+    b = _bench()
+    root = tmp_path / "repo"
+    csrc = root / "paper_1410_4876_gb300" / "csrc"
+    shutil.copytree(os.path.join(ROOT, "paper_1410_4876_gb300", "csrc"), csrc)
+    monkeypatch.setattr(b, "ROOT", str(root))
+    kinds = ("engine_kernel<Multi,256>", "engine_kernel<Bitset1,256>", "engine_kernel<Csr16,256>")
+    before = {k: b._engine_fingerprint(k) for k in kinds}
+    assert len(set(before.values())) == 3
+    with open(csrc / "cc_expand_multi.cuh", "a") as f:
+        f.write("\n// a comment changes nothing\n")
+    assert {k: b._engine_fingerprint(k) for k in kinds} == before
+    with open(csrc / "cc_expand_multi.cuh", "a") as f:
+        f.write("\nstatic_assert(true, \"\");\n")
+    after = {k: b._engine_fingerprint(k) for k in kinds}
+    assert after[kinds[0]] != before[kinds[0]]
+    assert after[kinds[1]] == before[kinds[1]] and after[kinds[2]] == before[kinds[2]]
