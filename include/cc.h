@@ -86,7 +86,9 @@ typedef struct cc_options {
   uint32_t spin_limit;         /* grid-barrier wait limit in polls; 0 = default (~8 s)    */
   uint32_t flags;              /* CC_FLAG_*                                               */
   uint32_t paths_per_thread;   /* bitset and batch expansion: paths a thread takes per    */
-                               /* round, 1..3; 0 = the build's default for the path       */
+                               /* round, 1..4 (one-word rows; fewer for wider rows and    */
+                               /* the batch, larger values take the most); 0 = the        */
+                               /* build's default for the path                            */
   uint32_t small_phase_paths;  /* bitset graphs: the cluster phase expands levels (or     */
                                /* chunks) of at most this many paths.  0 = 2 * cluster    */
                                /* size * 1024 for graphs of maximum degree <= 5, and no   */

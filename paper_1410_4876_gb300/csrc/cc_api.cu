@@ -25,7 +25,7 @@ using namespace cc;
 static bool options_valid(const cc_options& o) {
   if (o.threads_per_block && (o.threads_per_block < 64 || o.threads_per_block > 256 || o.threads_per_block % 32))
     return false;
-  if (o.mode > CC_MODE_CSR || o.blocks_per_sm > 4 || o.paths_per_thread > 3 || o.reserved) return false;
+  if (o.mode > CC_MODE_CSR || o.blocks_per_sm > 4 || o.paths_per_thread > 4 || o.reserved) return false;
   return true;
 }
 

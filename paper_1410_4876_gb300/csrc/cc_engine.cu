@@ -86,7 +86,7 @@ struct KindTraits {
       (K == Kind::Csr || K == Kind::Csr32) ? 2 : ((K == Kind::Csr16 || K == Kind::Bitset1) ? 3 : 4);
   // paths per thread per round of the flattened single-graph form (one slot atomic per
   // warp per round)
-  static constexpr int PF = K == Kind::Bitset1 ? 3 : (K == Kind::Bitset2 ? 2 : 1);
+  static constexpr int PF = K == Kind::Bitset1 ? 4 : (K == Kind::Bitset2 ? 2 : 1);
   // children staged per batch in a two-level step, in rounds of 32 (shared memory bound)
   static constexpr int PF2 = K == Kind::Bitset1 ? 4 : 1;
 };

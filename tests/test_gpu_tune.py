@@ -75,7 +75,7 @@ def test_replay_follows_length_and_options(cc):
             _same(lg.enumerate(), _ref(g))
 
 
-@pytest.mark.parametrize("pf", [1, 2, 3])
+@pytest.mark.parametrize("pf", [1, 2, 3, 4])
 @pytest.mark.parametrize("small", [0, 1024, 1 << 20])
 def test_paths_per_thread_and_small_phase(cc, pf, small):
     with cc.Context(frontier_bytes=1 << 30, paths_per_thread=pf, small_phase_paths=small) as ctx:
@@ -95,7 +95,7 @@ def test_launch_shapes(cc, tpb, bps):
 def test_set_options_validation(cc):
     with cc.Context(frontier_bytes=1 << 26) as ctx:
         o = cc.cc_options()
-        o.paths_per_thread = 4
+        o.paths_per_thread = 5
         assert cc.cc_context_set_options(ctx.handle, o) == cc.CC_ERR_ARG
         o.paths_per_thread = 0
         o.threads_per_block = 96 + 1
